@@ -1,0 +1,159 @@
+/*
+ * bcfmm — boundary-concentrated fast multipole evaluation of the Laplace
+ * volume potential on one GB300 (sm_103a).
+ *
+ * Method: Mohyaddin & Tausch, "A fast method for evaluating volume
+ * potentials in the Galerkin boundary element method" (arXiv 2112.00864).
+ *
+ *   VtV  u_t = int_t  int_Omega G(x,y) f(y) dy dx   for every tet t     (Sec. 1, task 1; Algorithm 1)
+ *   VtB  u_g = int_g  int_Omega G(x,y) f(y) dy ds   for every triangle g (task 2; Algorithm 2)
+ *   BtV  u_t = int_t  int_Gamma G(x,y) g(y) ds dx   for every tet t      (task 3; Algorithm 3,
+ *                                                                         single-layer part)
+ * with G(x,y) = 1/(4 pi |x-y|) (Sec. 1.1) and piecewise-constant (P0)
+ * densities and test functions (Sec. 1.2, Eq. galerkin:vol with p = 0).
+ *
+ * Discrete operator (identical to the FP64 CPU oracle's definition):
+ *   far element pairs : 4-point tet / 3-point triangle product rule
+ *   near element pairs: eta(t,s) = (rho_t + rho_s)/|x_t - x_s| > eta_ns
+ *                       (Eq. def:diam, Eq. def:sepRatio with centroids) use
+ *                       the near rule: closed-form potential of the uniform
+ *                       source element, composite collapsed Gauss-Legendre
+ *                       over the target element (near_n nodes per direction,
+ *                       near_k uniform refinements).
+ * The far field goes through truncated Cartesian Taylor expansions of order
+ * p (Sec. 3.3) on an adaptive octree of quadrature points (<= leaf_size
+ * points per leaf); interaction lists are the children of the parent's
+ * neighbours that are not neighbours (Sec. 2), and the near field of a leaf
+ * is its extended neighbour list N* (Sec. 3, Lemma 3.1).
+ *
+ * Conventions for every entry point:
+ *  - Return value is a bcfmm_status; nothing throws across this boundary.
+ *    On failure, bcfmm_last_error() returns a message (thread-local).
+ *  - The caller owns every pointer it passes.  The library copies the mesh
+ *    at build time and never keeps a caller pointer after a call returns.
+ *  - A context is bound to the CUDA device current at build time and to the
+ *    stream given there; all its device work is ordered on that stream.  It
+ *    is not thread-safe: one host thread at a time per context.
+ *  - Element order in inputs and outputs is the caller's.  Outputs are FP64
+ *    in every precision mode.
+ */
+#ifndef BCFMM_H
+#define BCFMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bcfmm_ctx bcfmm_ctx;
+
+typedef enum {
+  BCFMM_OK = 0,
+  BCFMM_ERR_ARG = -1,      /* bad argument (null pointer, size, parameter)      */
+  BCFMM_ERR_MESH = -2,     /* degenerate or non-finite element (index in msg)   */
+  BCFMM_ERR_CUDA = -3,     /* a CUDA call failed (message holds the CUDA error) */
+  BCFMM_ERR_OOM = -4,      /* device or host allocation failed                  */
+  BCFMM_ERR_TIMEOUT = -5,  /* a bounded device wait expired                     */
+  BCFMM_ERR_STATE = -6     /* call out of order (e.g. eval before set_density)  */
+} bcfmm_status;
+
+/* Arithmetic of the evaluation.  Setup (geometry, tree, near rule, tables)
+ * is FP64 in every mode. */
+typedef enum {
+  BCFMM_FP64 = 0,          /* plain: every pass in FP64 on CUDA cores              */
+  BCFMM_FP32 = 1,          /* P2P, P2M/M2M/L2L/L2P and M2L in FP32 (CUDA cores)     */
+  BCFMM_FP32_BF16X2 = 2,   /* FP32, M2L on tcgen05 tensor cores, BF16 hi+lo split
+                              (hi*hi + hi*lo + lo*hi), FP32 accumulation in TMEM   */
+  BCFMM_FP32_BF16X3 = 3    /* as above with a 3-term split (6 products)            */
+} bcfmm_precision;
+
+typedef enum { BCFMM_VOLUME = 0, BCFMM_BOUNDARY = 1 } bcfmm_density_kind;
+
+typedef struct {
+  int32_t p;            /* expansion order (total degree), 0..12; default 6            */
+  int32_t leaf_size;    /* max points per octree leaf (tet + triangle points); 64       */
+  double eta_ns;        /* near-pair threshold; default 1 - 2^-20 (all touching pairs)  */
+  int32_t near_n;       /* near rule: Gauss-Legendre nodes per direction; default 3     */
+  int32_t near_k;       /* near rule: uniform refinements of the target; default 1      */
+  int32_t precision;    /* bcfmm_precision; default BCFMM_FP64                          */
+  int32_t timing;       /* nonzero: record per-stage CUDA-event times of each eval      */
+} bcfmm_params;
+
+/* Fills *prm with the defaults above.  Never fails. */
+void bcfmm_default_params(bcfmm_params* prm);
+
+/*
+ * Build the context for one mesh: quadrature points (Sec. 1.2), the octree,
+ * interaction and extended neighbour lists (Sec. 2, Sec. 3), the near-pair
+ * list and its FP64 corrections N_ts - Q_ts (near rule minus product rule),
+ * and the translation tables (Sec. 3.3).
+ *   verts  [nvert][3] FP64, host memory
+ *   tets   [ntet][4]  int32 vertex ids, host memory (ntet >= 1)
+ *   tris   [ntri][3]  int32 vertex ids, host memory (ntri >= 0)
+ *   stream cudaStream_t (NULL = legacy default stream) used for all work
+ * Errors: BCFMM_ERR_ARG (null pointers, ids out of range, bad params),
+ * BCFMM_ERR_MESH (zero-volume tet / zero-area triangle / non-finite
+ * coordinate; the element index is in the message), BCFMM_ERR_OOM,
+ * BCFMM_ERR_CUDA.  On error *out is NULL.
+ */
+int bcfmm_build_bc_tree(const double* verts, int64_t nvert,
+                        const int32_t* tets, int64_t ntet,
+                        const int32_t* tris, int64_t ntri,
+                        const bcfmm_params* prm, void* stream, bcfmm_ctx** out);
+
+/*
+ * Set the P0 density coefficients (one value per element, Sec. 1.2).
+ *   kind   BCFMM_VOLUME: vals [ndens][ntet] (f of VtV/VtB);
+ *          BCFMM_BOUNDARY: vals [ndens][ntri] (g of BtV)
+ *   vals   FP64; device memory if is_device != 0 (read on the context's
+ *          stream before this call returns control of the buffer to the
+ *          stream order), else host memory (copied synchronously)
+ *   ndens  number of densities evaluated together, 1..16
+ * Errors: BCFMM_ERR_ARG, BCFMM_ERR_MESH (non-finite value), BCFMM_ERR_CUDA.
+ */
+int bcfmm_set_density(bcfmm_ctx* ctx, int32_t kind, const double* vals,
+                      int32_t ndens, int32_t is_device);
+
+/*
+ * Evaluate one task (Algorithms 1, 2, 3).  The work is enqueued on the
+ * context's stream.
+ *   out    FP64 [ndens][ntet] (VtV, BtV) or [ndens][ntri] (VtB); device memory
+ *          if out_is_device != 0 (written asynchronously on the stream),
+ *          else host memory (the call synchronises the stream before return)
+ * Errors: BCFMM_ERR_STATE (density of the needed kind not set),
+ * BCFMM_ERR_ARG, BCFMM_ERR_CUDA.
+ */
+int bcfmm_eval_vtv(bcfmm_ctx* ctx, double* out, int32_t out_is_device);
+int bcfmm_eval_vtb(bcfmm_ctx* ctx, double* out, int32_t out_is_device);
+int bcfmm_eval_btv(bcfmm_ctx* ctx, double* out, int32_t out_is_device);
+
+/*
+ * Context statistics as one JSON object (points, boxes, levels, list sizes,
+ * near pairs, setup seconds, last eval's stage times in ms when timing is
+ * on).  Writes at most cap bytes including the terminating NUL.
+ * Errors: BCFMM_ERR_ARG (null, or cap too small: the message gives the size).
+ */
+int bcfmm_stats(const bcfmm_ctx* ctx, char* json, size_t cap);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char* bcfmm_last_error(void);
+
+/* Release every resource of the context (synchronises its stream). NULL is a no-op. */
+void bcfmm_destroy(bcfmm_ctx* ctx);
+
+/*
+ * Test hook: the box-scaled M2L matrix of Sec. 3.3 that the library uses,
+ * for integer offset o = (x_t - x_s)/s between same-level box centres:
+ *   T[a][b] = D^{a+b}G(o) (-1)^{|b|} / (a! b!),   G = 1/(4 pi |.|),
+ * for |a| + |b| <= p (zero otherwise), multi-indices ordered by total
+ * degree, then lexicographically descending.  T: host [np][np], np =
+ * (p+1)(p+2)(p+3)/6.  Errors: BCFMM_ERR_ARG.
+ */
+int bcfmm_debug_m2l_matrix(int32_t p, const double* o, double* T);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BCFMM_H */

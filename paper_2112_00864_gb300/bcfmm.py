@@ -1,0 +1,178 @@
+"""Thin Python binding of the bcfmm C ABI (``include/bcfmm.h``).
+
+Argument marshalling only: every step of the evaluation runs in the CUDA
+library ``_build/libbcfmm.so``.  PyTorch supplies device memory and the CUDA
+stream.  There is no CPU fallback: loading fails loudly when the library is
+missing (build it with ``paper_2112_00864_gb300.build.build()``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import json
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libbcfmm.so")
+
+BCFMM_OK = 0
+STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_MESH", -3: "ERR_CUDA", -4: "ERR_OOM", -5: "ERR_TIMEOUT", -6: "ERR_STATE"}
+PRECISION = {"fp64": 0, "fp32": 1, "bf16x2": 2, "bf16x3": 3}
+VOLUME, BOUNDARY = 0, 1
+EXPORTED = ["bcfmm_default_params", "bcfmm_build_bc_tree", "bcfmm_set_density", "bcfmm_eval_vtv",
+            "bcfmm_eval_vtb", "bcfmm_eval_btv", "bcfmm_stats", "bcfmm_last_error", "bcfmm_destroy",
+            "bcfmm_debug_m2l_matrix"]
+
+
+class Params(C.Structure):
+    _fields_ = [("p", C.c_int32), ("leaf_size", C.c_int32), ("eta_ns", C.c_double), ("near_n", C.c_int32),
+                ("near_k", C.c_int32), ("precision", C.c_int32), ("timing", C.c_int32)]
+
+
+class BcfmmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise ImportError(f"bcfmm CUDA library not built: {path} is missing "
+                              "(run paper_2112_00864_gb300.build.build())")
+        L = C.CDLL(path)
+        p, i32, i64, d = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+        L.bcfmm_default_params.argtypes = [C.POINTER(Params)]
+        L.bcfmm_default_params.restype = None
+        L.bcfmm_build_bc_tree.argtypes = [p, i64, p, i64, p, i64, C.POINTER(Params), p, C.POINTER(p)]
+        L.bcfmm_build_bc_tree.restype = C.c_int
+        L.bcfmm_set_density.argtypes = [p, i32, p, i32, i32]
+        L.bcfmm_set_density.restype = C.c_int
+        for f in ("bcfmm_eval_vtv", "bcfmm_eval_vtb", "bcfmm_eval_btv"):
+            getattr(L, f).argtypes = [p, p, i32]
+            getattr(L, f).restype = C.c_int
+        L.bcfmm_stats.argtypes = [p, C.c_char_p, C.c_size_t]
+        L.bcfmm_stats.restype = C.c_int
+        L.bcfmm_last_error.argtypes = []
+        L.bcfmm_last_error.restype = C.c_char_p
+        L.bcfmm_destroy.argtypes = [p]
+        L.bcfmm_destroy.restype = None
+        L.bcfmm_debug_m2l_matrix.argtypes = [i32, p, p]
+        L.bcfmm_debug_m2l_matrix.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != BCFMM_OK:
+        raise BcfmmError(rc, load().bcfmm_last_error().decode())
+
+
+def default_params(**kw) -> Params:
+    prm = Params()
+    load().bcfmm_default_params(C.byref(prm))
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = PRECISION[v]
+        setattr(prm, k, v)
+    return prm
+
+
+def nterms(p: int) -> int:
+    return (p + 1) * (p + 2) * (p + 3) // 6
+
+
+def debug_m2l_matrix(p: int, o) -> np.ndarray:
+    o = np.ascontiguousarray(o, np.float64)
+    T = np.zeros((nterms(p), nterms(p)))
+    _check(load().bcfmm_debug_m2l_matrix(p, o.ctypes.data, T.ctypes.data))
+    return T
+
+
+def _ptr(x):
+    """(address, is_device) of a numpy array or torch tensor."""
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data, 0
+    return x.data_ptr(), int(x.is_cuda)
+
+
+class Context:
+    """One mesh on the current CUDA device, bound to ``stream`` (a
+    torch.cuda.Stream, an int handle, or None for the current torch stream)."""
+
+    def __init__(self, verts, tets, tris, params: Params | None = None, stream=None, **kw):
+        import torch
+        self._lib = load()
+        self.params = params if params is not None else default_params(**kw)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        handle = stream if isinstance(stream, int) else stream.cuda_stream
+        self._v = np.ascontiguousarray(verts, np.float64)
+        self._t = np.ascontiguousarray(tets, np.int32)
+        self._f = np.ascontiguousarray(tris, np.int32) if tris is not None else np.zeros((0, 3), np.int32)
+        self.ntet, self.ntri = self._t.shape[0], self._f.shape[0]
+        ctx = C.c_void_p()
+        _check(self._lib.bcfmm_build_bc_tree(self._v.ctypes.data, self._v.shape[0], self._t.ctypes.data, self.ntet,
+                                             self._f.ctypes.data, self.ntri, C.byref(self.params),
+                                             C.c_void_p(handle), C.byref(ctx)))
+        self._ctx = ctx
+        self.ndens = {VOLUME: 0, BOUNDARY: 0}
+
+    @classmethod
+    def from_mesh(cls, mesh, **kw):
+        return cls(mesh.verts, mesh.tets, mesh.tris, **kw)
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            self._lib.bcfmm_destroy(self._ctx)
+            self._ctx = None
+
+    __del__ = close
+
+    def set_density(self, kind: int, vals):
+        """vals: [ndens, nelem] float64 numpy array (host) or CUDA tensor (device)."""
+        if isinstance(vals, np.ndarray):
+            vals = np.ascontiguousarray(np.atleast_2d(vals), np.float64)
+            nd = vals.shape[0]
+        else:
+            if vals.dim() == 1:
+                vals = vals[None]
+            vals = vals.contiguous()
+            assert vals.dtype.is_floating_point and vals.element_size() == 8, "densities must be float64"
+            nd = vals.shape[0]
+        self._dens_keep = vals
+        ptr, dev = _ptr(vals)
+        _check(self._lib.bcfmm_set_density(self._ctx, kind, C.c_void_p(ptr), nd, dev))
+        self.ndens[kind] = nd
+
+    def _eval(self, fn, nel: int, kind: int, out=None):
+        nd = self.ndens[kind]
+        if out is None:
+            import torch
+            out = torch.empty((nd, nel), dtype=torch.float64, device="cuda")
+        ptr, dev = _ptr(out)
+        _check(fn(self._ctx, C.c_void_p(ptr), dev))
+        return out
+
+    def eval_vtv(self, out=None):
+        return self._eval(self._lib.bcfmm_eval_vtv, self.ntet, VOLUME, out)
+
+    def eval_vtb(self, out=None):
+        return self._eval(self._lib.bcfmm_eval_vtb, self.ntri, VOLUME, out)
+
+    def eval_btv(self, out=None):
+        return self._eval(self._lib.bcfmm_eval_btv, self.ntet, BOUNDARY, out)
+
+    def eval(self, task: str, out=None):
+        return {"vtv": self.eval_vtv, "vtb": self.eval_vtb, "btv": self.eval_btv}[task](out)
+
+    def stats(self) -> dict:
+        buf = C.create_string_buffer(1 << 16)
+        _check(self._lib.bcfmm_stats(self._ctx, buf, len(buf)))
+        return json.loads(buf.value.decode())

@@ -1,0 +1,578 @@
+// C ABI of the bcfmm library: context setup (mesh, tree, lists, near-rule
+// corrections, translation tables) and the VtV / VtB / BtV evaluations
+// (Algorithms 1-3 of arXiv 2112.00864).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/bcfmm.h"
+#include "internal.h"
+#include "kernels.cuh"
+#include "m2l_tc.cuh"
+
+using namespace bcfmm;
+
+static thread_local std::string g_err;
+
+static int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define CU(call)                                                                            \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess) {                                                                \
+      if (e_ == cudaErrorMemoryAllocation) return fail(BCFMM_ERR_OOM, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+      return fail(BCFMM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));     \
+    }                                                                                       \
+  } while (0)
+
+namespace {
+
+struct DevAlloc {
+  std::vector<void*> ptrs;
+  template <typename T>
+  cudaError_t alloc(T** p, size_t n) {
+    *p = nullptr;
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+    if (e == cudaSuccess) ptrs.push_back(*p);
+    return e;
+  }
+  template <typename T>
+  cudaError_t upload(T** p, const T* h, size_t n, cudaStream_t st) {
+    cudaError_t e = alloc(p, n);
+    if (e != cudaSuccess || n == 0) return e;
+    return cudaMemcpyAsync(*p, h, n * sizeof(T), cudaMemcpyHostToDevice, st);
+  }
+  void release(void* p) {
+    auto it = std::find(ptrs.begin(), ptrs.end(), p);
+    if (it != ptrs.end()) { cudaFree(*it); ptrs.erase(it); }
+  }
+  void free_all() {
+    for (void* p : ptrs) cudaFree(p);
+    ptrs.clear();
+  }
+};
+
+struct TaskDev {
+  DevTaskLists L{};
+  std::vector<int> m2m_off, l2l_off;   // host offsets into the per-level arrays
+  int* m2m_parent = nullptr;
+  int* l2l_child = nullptr;
+  int64_t p2p_pairs = 0, near_boxes = 0, m2l_pairs = 0, nnz = 0;
+};
+
+}  // namespace
+
+struct bcfmm_ctx {
+  int device = 0;
+  cudaStream_t st = nullptr;
+  bcfmm_params prm{};
+  int np = 0;
+  int nlevels = 0, nbox = 0, nleaf = 0;
+  int64_t ntet = 0, ntri = 0, npts[2] = {0, 0};
+  DevAlloc mem;
+  DevGeom G{};
+  TaskDev task[3];
+  // translation tables
+  double *T64 = nullptr, *M2M64 = nullptr, *L2L64 = nullptr;
+  float *T32 = nullptr, *M2M32 = nullptr, *L2L32 = nullptr;
+  M2LTensorTables tc{};
+  // densities
+  int ndens[2] = {0, 0}, ndp[2] = {0, 0};
+  double* dens[2] = {nullptr, nullptr};
+  // work buffers (sized for the largest ndp seen)
+  int work_ndp = 0;
+  double *W64 = nullptr, *mom64 = nullptr, *loc64 = nullptr, *phi = nullptr, *out_dev = nullptr;
+  float *W32 = nullptr, *mom32 = nullptr, *loc32 = nullptr;
+  // stats
+  double sec_setup = 0, sec_tree = 0, sec_lists = 0, sec_near_host = 0, sec_near_dev = 0;
+  std::vector<int> leaves_per_level, boxes_per_level;
+  float stage_ms[8] = {0};
+  cudaEvent_t ev[9] = {};
+  bool ev_ok = false;
+};
+
+static double wall() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+static int pad_ndens(int n) {
+  int p = 1;
+  while (p < n) p <<= 1;
+  return p;
+}
+
+extern "C" void bcfmm_default_params(bcfmm_params* prm) {
+  if (!prm) return;
+  prm->p = 6;
+  prm->leaf_size = 64;
+  prm->eta_ns = 1.0 - std::ldexp(1.0, -20);
+  prm->near_n = 3;
+  prm->near_k = 1;
+  prm->precision = BCFMM_FP64;
+  prm->timing = 0;
+}
+
+extern "C" const char* bcfmm_last_error(void) { return g_err.c_str(); }
+
+extern "C" int bcfmm_debug_m2l_matrix(int32_t p, const double* o, double* T) {
+  if (p < 0 || p > kMaxP || !o || !T) return fail(BCFMM_ERR_ARG, "debug_m2l_matrix: bad argument");
+  m2l_matrix_scaled(p, o, T);
+  return BCFMM_OK;
+}
+
+static int upload_task(bcfmm_ctx* C, const HostSetup& H, int t) {
+  const HostTask& T = H.task[t];
+  TaskDev& D = C->task[t];
+  DevTaskLists& L = D.L;
+  cudaStream_t st = C->st;
+  auto& m = C->mem;
+  L.src_cls = T.src_cls;
+  L.tgt_cls = T.tgt_cls;
+  L.n_p2p = (int)T.p2p_leaf.size();
+  int *p2p_leaf, *near_off, *near_box, *m2l_tgt, *vl_off, *vl_src, *p2m_leaf, *l2p_leaf;
+  uint16_t* vl_code;
+  CU(m.upload(&p2p_leaf, T.p2p_leaf.data(), T.p2p_leaf.size(), st));
+  CU(m.upload(&near_off, T.near_off.data(), T.near_off.size(), st));
+  CU(m.upload(&near_box, T.near_box.data(), T.near_box.size(), st));
+  L.p2p_leaf = p2p_leaf; L.near_off = near_off; L.near_box = near_box;
+  L.n_m2l = (int)T.m2l_tgt.size();
+  CU(m.upload(&m2l_tgt, T.m2l_tgt.data(), T.m2l_tgt.size(), st));
+  CU(m.upload(&vl_off, T.vl_off.data(), T.vl_off.size(), st));
+  CU(m.upload(&vl_src, T.vl_src.data(), T.vl_src.size(), st));
+  CU(m.upload(&vl_code, T.vl_code.data(), T.vl_code.size(), st));
+  L.m2l_tgt = m2l_tgt; L.vl_off = vl_off; L.vl_src = vl_src; L.vl_code = vl_code;
+  L.n_p2m = (int)T.p2m_leaf.size();
+  CU(m.upload(&p2m_leaf, T.p2m_leaf.data(), T.p2m_leaf.size(), st));
+  L.p2m_leaf = p2m_leaf;
+  L.n_l2p = (int)T.l2p_leaf.size();
+  CU(m.upload(&l2p_leaf, T.l2p_leaf.data(), T.l2p_leaf.size(), st));
+  L.l2p_leaf = l2p_leaf;
+  // per-level lists
+  std::vector<int> flat;
+  D.m2m_off.assign(1, 0);
+  for (auto& v : T.m2m_parent) { flat.insert(flat.end(), v.begin(), v.end()); D.m2m_off.push_back((int)flat.size()); }
+  CU(m.upload(&D.m2m_parent, flat.data(), flat.size(), st));
+  flat.clear();
+  D.l2l_off.assign(1, 0);
+  for (auto& v : T.l2l_child) { flat.insert(flat.end(), v.begin(), v.end()); D.l2l_off.push_back((int)flat.size()); }
+  CU(m.upload(&D.l2l_child, flat.data(), flat.size(), st));
+  // target elements: sorted positions of their points
+  const int tc = T.tgt_cls, sc = T.src_cls;
+  const int nqt = tc == 0 ? 4 : 3;
+  const int64_t nte = tc == 0 ? H.ntet : H.ntri;
+  L.ntgt_el = nte;
+  L.nsrc_el = sc == 0 ? H.ntet : H.ntri;
+  L.nq_tgt = nqt;
+  std::vector<int> pos_of(H.perm[tc].size());
+  for (size_t j = 0; j < pos_of.size(); ++j) pos_of[H.perm[tc][j]] = (int)j;
+  std::vector<int> ep(4 * nte, -1);
+  for (int64_t e = 0; e < nte; ++e)
+    for (int q = 0; q < nqt; ++q) ep[4 * e + q] = pos_of[nqt * e + q];
+  int* elem_pts;
+  CU(m.upload(&elem_pts, ep.data(), ep.size(), st));
+  L.elem_pts = elem_pts;
+  // near pairs + FP64 corrections computed on the device
+  int64_t *cor_off;
+  int *cor_col, *cor_row;
+  double* cor_val;
+  D.nnz = (int64_t)T.cor_col.size();
+  CU(m.upload(&cor_off, T.cor_off.data(), T.cor_off.size(), st));
+  CU(m.upload(&cor_col, T.cor_col.data(), T.cor_col.size(), st));
+  std::vector<int> row(T.cor_col.size());
+  for (int64_t e = 0; e < nte; ++e)
+    for (int64_t k = T.cor_off[e]; k < T.cor_off[e + 1]; ++k) row[k] = (int)e;
+  CU(m.upload(&cor_row, row.data(), row.size(), st));
+  CU(m.alloc(&cor_val, T.cor_col.size()));
+  L.cor_off = cor_off; L.cor_col = cor_col; L.cor_val = cor_val;
+  {
+    double *tv, *sv, *tqp, *tqw, *sqp, *sqw, *glx, *glw;
+    const std::vector<double>& TV = tc == 0 ? H.tet_v : H.tri_v;
+    const std::vector<double>& SV = sc == 0 ? H.tet_v : H.tri_v;
+    CU(m.upload(&tv, TV.data(), TV.size(), st));
+    CU(m.upload(&sv, SV.data(), SV.size(), st));
+    CU(m.upload(&tqp, H.qp[tc].data(), H.qp[tc].size(), st));
+    CU(m.upload(&tqw, H.qw[tc].data(), H.qw[tc].size(), st));
+    CU(m.upload(&sqp, H.qp[sc].data(), H.qp[sc].size(), st));
+    CU(m.upload(&sqw, H.qw[sc].data(), H.qw[sc].size(), st));
+    std::vector<double> gx, gw;
+    gauss_legendre01(C->prm.near_n, gx, gw);
+    CU(m.upload(&glx, gx.data(), gx.size(), st));
+    CU(m.upload(&glw, gw.data(), gw.size(), st));
+    CU(launch_near_rule(t, D.nnz, cor_row, cor_col, tv, sv, tqp, tqw, sqp, sqw, glx, glw, C->prm.near_n,
+                        C->prm.near_k, cor_val, st));
+    CU(cudaStreamSynchronize(st));
+    for (void* p : {(void*)tv, (void*)sv, (void*)tqp, (void*)tqw, (void*)sqp, (void*)sqw, (void*)glx, (void*)glw,
+                    (void*)cor_row})
+      m.release(p);
+  }
+  // counts for the statistics and the roofline
+  D.near_boxes = (int64_t)T.near_box.size();
+  D.m2l_pairs = (int64_t)T.vl_src.size();
+  D.p2p_pairs = 0;
+  for (size_t i = 0; i < T.p2p_leaf.size(); ++i) {
+    const HostBox& B = H.box[T.p2p_leaf[i]];
+    int64_t nt = B.pt1[tc] - B.pt0[tc], ns = 0;
+    for (int k = T.near_off[i]; k < T.near_off[i + 1]; ++k) {
+      const HostBox& S = H.box[T.near_box[k]];
+      ns += S.pt1[sc] - S.pt0[sc];
+    }
+    D.p2p_pairs += nt * ns;
+  }
+  return BCFMM_OK;
+}
+
+static int build_impl(const double* verts, int64_t nvert, const int32_t* tets, int64_t ntet, const int32_t* tris,
+                      int64_t ntri, const bcfmm_params* prm_in, void* stream, bcfmm_ctx** out) {
+  double t0 = wall();
+  bcfmm_params prm;
+  bcfmm_default_params(&prm);
+  if (prm_in) prm = *prm_in;
+  if (!out) return fail(BCFMM_ERR_ARG, "build_bc_tree: out is NULL");
+  *out = nullptr;
+  if (!verts || !tets || nvert <= 0 || ntet <= 0 || ntri < 0 || (ntri > 0 && !tris))
+    return fail(BCFMM_ERR_ARG, "build_bc_tree: null mesh arrays or empty mesh");
+  if (4 * ntet > INT32_MAX / 2 || 3 * ntri > INT32_MAX / 2) return fail(BCFMM_ERR_ARG, "build_bc_tree: mesh too large");
+  if (prm.p < 0 || prm.p > kMaxP) return fail(BCFMM_ERR_ARG, "build_bc_tree: p must be in 0..12");
+  if (prm.leaf_size < 1 || prm.leaf_size > 128) return fail(BCFMM_ERR_ARG, "build_bc_tree: leaf_size must be in 1..128");
+  if (!(prm.eta_ns > 0)) return fail(BCFMM_ERR_ARG, "build_bc_tree: eta_ns must be > 0");
+  if (prm.near_n < 1 || prm.near_n > 8 || prm.near_k < 0 || prm.near_k > 3)
+    return fail(BCFMM_ERR_ARG, "build_bc_tree: near_n must be in 1..8 and near_k in 0..3");
+  if (prm.precision < BCFMM_FP64 || prm.precision > BCFMM_FP32_BF16X3)
+    return fail(BCFMM_ERR_ARG, "build_bc_tree: unknown precision");
+  if ((prm.precision == BCFMM_FP32_BF16X2 || prm.precision == BCFMM_FP32_BF16X3) && !m2l_tc_supported(prm.p))
+    return fail(BCFMM_ERR_ARG, "build_bc_tree: the tensor-core M2L supports p <= " + std::to_string(kTcMaxP));
+
+  HostSetup H;
+  bool mesh_err = false;
+  std::string e = setup_mesh(H, verts, nvert, tets, ntet, tris, ntri, &mesh_err);
+  if (!e.empty()) return fail(mesh_err ? BCFMM_ERR_MESH : BCFMM_ERR_ARG, "build_bc_tree: " + e);
+
+  int dev = 0;
+  CU(cudaGetDevice(&dev));
+  bcfmm_ctx* C = new bcfmm_ctx();
+  C->device = dev;
+  C->st = (cudaStream_t)stream;
+  C->prm = prm;
+  C->ntet = ntet;
+  C->ntri = ntri;
+  auto cleanup = [&](int code) { C->mem.free_all(); delete C; return code; };
+
+  build_tree(H, prm.leaf_size);
+  for (auto& B : H.box)
+    if (!B.nchild && (B.pt1[0] - B.pt0[0] > 128 || B.pt1[1] - B.pt0[1] > 128))
+      return cleanup(fail(BCFMM_ERR_MESH, "build_bc_tree: more than 128 coincident points in one leaf at the deepest level"));
+  build_lists(H);
+  find_near_pairs(H, prm.eta_ns);
+  C->sec_tree = H.seconds_tree;
+  C->sec_lists = H.seconds_lists;
+  C->sec_near_host = H.seconds_near;
+  C->nlevels = H.nlevels;
+  C->nbox = (int)H.box.size();
+  C->np = nterms(prm.p);
+  C->leaves_per_level.assign(H.nlevels, 0);
+  C->boxes_per_level.assign(H.nlevels, 0);
+  for (auto& B : H.box) { C->boxes_per_level[B.level]++; if (!B.nchild) { C->leaves_per_level[B.level]++; C->nleaf++; } }
+
+  cudaStream_t st = C->st;
+  auto& m = C->mem;
+  DevGeom& G = C->G;
+  G.np = C->np; G.p = prm.p; G.nbox = C->nbox;
+  {
+    MultiIndex M; M.init(prm.p);
+    std::vector<int> mi(M.n), tk(M.n);
+    for (int q = 0; q < M.n; ++q) {
+      mi[q] = M.a[q] | (M.b[q] << 8) | (M.c[q] << 16);
+      tk[q] = nterms(prm.p - (M.a[q] + M.b[q] + M.c[q]));
+    }
+    int *dmi, *dtk;
+    if (m.upload(&dmi, mi.data(), mi.size(), st) != cudaSuccess || m.upload(&dtk, tk.data(), tk.size(), st) != cudaSuccess)
+      return cleanup(fail(BCFMM_ERR_OOM, "build_bc_tree: device allocation failed"));
+    G.mi = dmi; G.tri_k = dtk;
+  }
+  // boxes
+  {
+    const int nb = C->nbox;
+    std::vector<double4_32a> cs(nb);
+    std::vector<int> c0(nb), nc(nb), oc(nb), par(nb);
+    std::vector<int2> rg[2] = {std::vector<int2>(nb), std::vector<int2>(nb)};
+    for (int i = 0; i < nb; ++i) {
+      const HostBox& B = H.box[i];
+      cs[i] = make_double4_32a(B.c[0], B.c[1], B.c[2], B.s);
+      c0[i] = B.child0; nc[i] = B.nchild; oc[i] = B.octant; par[i] = B.parent;
+      for (int c = 0; c < 2; ++c) rg[c][i] = make_int2(B.pt0[c], B.pt1[c]);
+    }
+    double4_32a* dcs; int *dc0, *dnc, *doc, *dpar; int2 *drg0, *drg1;
+    bool ok = m.upload(&dcs, cs.data(), nb, st) == cudaSuccess && m.upload(&dc0, c0.data(), nb, st) == cudaSuccess &&
+              m.upload(&dnc, nc.data(), nb, st) == cudaSuccess && m.upload(&doc, oc.data(), nb, st) == cudaSuccess &&
+              m.upload(&dpar, par.data(), nb, st) == cudaSuccess && m.upload(&drg0, rg[0].data(), nb, st) == cudaSuccess &&
+              m.upload(&drg1, rg[1].data(), nb, st) == cudaSuccess;
+    if (!ok) return cleanup(fail(BCFMM_ERR_OOM, "build_bc_tree: device allocation failed (boxes)"));
+    G.box_cs = dcs; G.box_child0 = dc0; G.box_nchild = dnc; G.box_octant = doc; G.box_parent = dpar;
+    G.box_rng[0] = drg0; G.box_rng[1] = drg1;
+  }
+  // sorted points
+  for (int c = 0; c < 2; ++c) {
+    const int nq = c == 0 ? 4 : 3;
+    const int64_t n = (int64_t)H.perm[c].size();
+    C->npts[c] = n;
+    std::vector<double4_32a> p64(n);
+    std::vector<float4> hi(n), lo(n);
+    std::vector<int> el(n);
+    for (int64_t j = 0; j < n; ++j) {
+      const int o = H.perm[c][j];
+      const double* x = &H.qp[c][3 * (int64_t)o];
+      p64[j] = make_double4_32a(x[0], x[1], x[2], H.qw[c][o]);
+      float h[3], l[3];
+      for (int a = 0; a < 3; ++a) { h[a] = (float)x[a]; l[a] = (float)(x[a] - (double)h[a]); }
+      hi[j] = make_float4(h[0], h[1], h[2], (float)H.qw[c][o]);
+      lo[j] = make_float4(l[0], l[1], l[2], 0.f);
+      el[j] = o / nq;
+    }
+    double4_32a* dp; float4 *dh, *dl; int* de;
+    bool ok = m.upload(&dp, p64.data(), n, st) == cudaSuccess && m.upload(&dh, hi.data(), n, st) == cudaSuccess &&
+              m.upload(&dl, lo.data(), n, st) == cudaSuccess && m.upload(&de, el.data(), n, st) == cudaSuccess;
+    if (!ok) return cleanup(fail(BCFMM_ERR_OOM, "build_bc_tree: device allocation failed (points)"));
+    G.pt64[c] = dp; G.pthi[c] = dh; G.ptlo[c] = dl; G.pt_elem[c] = de;
+  }
+  // translation tables: M2L transposed per offset code, M2M / L2L per octant
+  {
+    const int np = C->np;
+    std::vector<double> T(kNumOffsets * (size_t)np * np, 0.0), Tt(kNumOffsets * (size_t)np * np, 0.0), tmp(np * np);
+    for (int code = 0; code < kNumOffsets; ++code) {
+      int o[3] = {code % 7 - 3, (code / 7) % 7 - 3, code / 49 - 3};
+      if (std::abs(o[0]) <= 1 && std::abs(o[1]) <= 1 && std::abs(o[2]) <= 1) continue;
+      double od[3] = {(double)o[0], (double)o[1], (double)o[2]};
+      m2l_matrix_scaled(prm.p, od, tmp.data());
+      for (int a = 0; a < np; ++a)
+        for (int b = 0; b < np; ++b) {
+          T[((size_t)code * np + a) * np + b] = tmp[a * np + b];
+          Tt[((size_t)code * np + b) * np + a] = tmp[a * np + b];
+        }
+    }
+    std::vector<double> Mm, Lm;
+    m2m_matrices(prm.p, Mm);
+    l2l_matrices(prm.p, Lm);
+    std::vector<float> Tt32(Tt.begin(), Tt.end()), M32(Mm.begin(), Mm.end()), L32(Lm.begin(), Lm.end());
+    bool ok = m.upload(&C->T64, Tt.data(), Tt.size(), st) == cudaSuccess &&
+              m.upload(&C->M2M64, Mm.data(), Mm.size(), st) == cudaSuccess &&
+              m.upload(&C->L2L64, Lm.data(), Lm.size(), st) == cudaSuccess &&
+              m.upload(&C->T32, Tt32.data(), Tt32.size(), st) == cudaSuccess &&
+              m.upload(&C->M2M32, M32.data(), M32.size(), st) == cudaSuccess &&
+              m.upload(&C->L2L32, L32.data(), L32.size(), st) == cudaSuccess;
+    if (!ok) return cleanup(fail(BCFMM_ERR_OOM, "build_bc_tree: device allocation failed (tables)"));
+    if (prm.precision == BCFMM_FP32_BF16X2 || prm.precision == BCFMM_FP32_BF16X3) {
+      cudaError_t ce = m2l_tc_prepare_tables(prm.p, T.data(), prm.precision == BCFMM_FP32_BF16X3 ? 3 : 2, &C->tc, st);
+      if (ce != cudaSuccess) return cleanup(fail(BCFMM_ERR_CUDA, std::string("build_bc_tree: tensor tables: ") + cudaGetErrorString(ce)));
+    }
+  }
+  double tn = wall();
+  for (int t = 0; t < 3; ++t) {
+    int rc = upload_task(C, H, t);
+    if (rc != BCFMM_OK) return cleanup(rc);
+  }
+  C->sec_near_dev = wall() - tn;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return cleanup(fail(BCFMM_ERR_CUDA, "build_bc_tree: stream sync failed"));
+  if (prm.timing) {
+    C->ev_ok = true;
+    for (auto& ev : C->ev) if (cudaEventCreate(&ev) != cudaSuccess) C->ev_ok = false;
+  }
+  C->sec_setup = wall() - t0;
+  *out = C;
+  return BCFMM_OK;
+}
+
+extern "C" int bcfmm_build_bc_tree(const double* verts, int64_t nvert, const int32_t* tets, int64_t ntet,
+                                   const int32_t* tris, int64_t ntri, const bcfmm_params* prm, void* stream,
+                                   bcfmm_ctx** out) {
+  try {
+    return build_impl(verts, nvert, tets, ntet, tris, ntri, prm, stream, out);
+  } catch (const std::bad_alloc&) {
+    return fail(BCFMM_ERR_OOM, "build_bc_tree: host allocation failed");
+  } catch (const std::exception& ex) {
+    return fail(BCFMM_ERR_ARG, std::string("build_bc_tree: ") + ex.what());
+  }
+}
+
+static int ensure_work(bcfmm_ctx* C, int ndp) {
+  if (C->work_ndp >= ndp) return BCFMM_OK;
+  auto& m = C->mem;
+  for (void* p : {(void*)C->W64, (void*)C->mom64, (void*)C->loc64, (void*)C->phi, (void*)C->out_dev, (void*)C->W32,
+                  (void*)C->mom32, (void*)C->loc32})
+    if (p) m.release(p);
+  const int64_t npmax = std::max(C->npts[0], C->npts[1]);
+  const int64_t nel = std::max(C->ntet, C->ntri);
+  const size_t nexp = (size_t)C->nbox * ndp * C->np;
+  const bool f64 = C->prm.precision == BCFMM_FP64;
+  CU(m.alloc(&C->phi, (size_t)ndp * npmax));
+  CU(m.alloc(&C->out_dev, (size_t)ndp * nel));
+  if (f64) {
+    CU(m.alloc(&C->W64, (size_t)ndp * npmax));
+    CU(m.alloc(&C->mom64, nexp));
+    CU(m.alloc(&C->loc64, nexp));
+    C->W32 = C->mom32 = C->loc32 = nullptr;
+  } else {
+    CU(m.alloc(&C->W32, (size_t)ndp * npmax));
+    CU(m.alloc(&C->mom32, nexp));
+    CU(m.alloc(&C->loc32, nexp));
+    C->W64 = C->mom64 = C->loc64 = nullptr;
+  }
+  C->work_ndp = ndp;
+  return BCFMM_OK;
+}
+
+extern "C" int bcfmm_set_density(bcfmm_ctx* C, int32_t kind, const double* vals, int32_t ndens, int32_t is_device) {
+  if (!C || !vals) return fail(BCFMM_ERR_ARG, "set_density: null argument");
+  if (kind != BCFMM_VOLUME && kind != BCFMM_BOUNDARY) return fail(BCFMM_ERR_ARG, "set_density: unknown kind");
+  if (ndens < 1 || ndens > 16) return fail(BCFMM_ERR_ARG, "set_density: ndens must be in 1..16");
+  const int64_t nel = kind == BCFMM_VOLUME ? C->ntet : C->ntri;
+  if (nel == 0) return fail(BCFMM_ERR_ARG, "set_density: the mesh has no elements of this kind");
+  const size_t n = (size_t)ndens * nel;
+  if (!is_device)
+    for (size_t i = 0; i < n; ++i)
+      if (!std::isfinite(vals[i])) return fail(BCFMM_ERR_MESH, "set_density: value " + std::to_string(i) + " is not finite");
+  if (C->ndens[kind] < ndens) {
+    if (C->dens[kind]) C->mem.release(C->dens[kind]);
+    C->dens[kind] = nullptr;
+    CU(C->mem.alloc(&C->dens[kind], (size_t)16 * nel));
+  }
+  CU(cudaMemcpyAsync(C->dens[kind], vals, n * sizeof(double), is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                     C->st));
+  if (!is_device) CU(cudaStreamSynchronize(C->st));
+  C->ndens[kind] = ndens;
+  C->ndp[kind] = pad_ndens(ndens);
+  return ensure_work(C, C->ndp[kind]);
+}
+
+static int eval_impl(bcfmm_ctx* C, int t, double* out, int out_is_device) {
+  if (!C || !out) return fail(BCFMM_ERR_ARG, "eval: null argument");
+  TaskDev& D = C->task[t];
+  const DevTaskLists& L = D.L;
+  const int kind = L.src_cls;     // class 0 sources: volume density; class 1: boundary density
+  if (C->ndens[kind] == 0)
+    return fail(BCFMM_ERR_STATE, kind == 0 ? "eval: volume density not set" : "eval: boundary density not set");
+  const int ndens = C->ndens[kind], ndp = C->ndp[kind];
+  const int rc = ensure_work(C, ndp);
+  if (rc != BCFMM_OK) return rc;
+  cudaStream_t st = C->st;
+  const DevGeom& G = C->G;
+  const int64_t nsp = C->npts[L.src_cls], ntp = C->npts[L.tgt_cls];
+  const int64_t nsel = kind == 0 ? C->ntet : C->ntri;
+  const size_t nexp = (size_t)C->nbox * ndp * C->np;
+  const bool f64 = C->prm.precision == BCFMM_FP64;
+  const bool tc = C->prm.precision == BCFMM_FP32_BF16X2 || C->prm.precision == BCFMM_FP32_BF16X3;
+  const bool tm = C->prm.timing && C->ev_ok;
+  double* outd = out_is_device ? out : C->out_dev;
+  if (tm) CU(cudaEventRecord(C->ev[0], st));
+  if (f64) {
+    CU(launch_weights<double>(G, L.src_cls, nsp, C->dens[kind], nsel, ndens, ndp, C->W64, st));
+    CU(cudaMemsetAsync(C->mom64, 0, nexp * sizeof(double), st));
+    CU(cudaMemsetAsync(C->loc64, 0, nexp * sizeof(double), st));
+    if (tm) CU(cudaEventRecord(C->ev[1], st));
+    CU(launch_p2m<double>(G, L, C->W64, nsp, ndp, C->mom64, st));
+    for (int l = C->nlevels - 1; l >= 0; --l) {
+      const int n = D.m2m_off[l + 1] - D.m2m_off[l];
+      CU(launch_m2m<double>(G, D.m2m_parent + D.m2m_off[l], n, C->M2M64, ndp, C->mom64, st));
+    }
+    if (tm) CU(cudaEventRecord(C->ev[2], st));
+    CU(launch_m2l_simt<double>(G, L, C->T64, G.tri_k, ndp, C->mom64, C->loc64, st));
+    if (tm) CU(cudaEventRecord(C->ev[3], st));
+    for (int l = 3; l < C->nlevels; ++l) {
+      const int n = D.l2l_off[l + 1] - D.l2l_off[l];
+      CU(launch_l2l<double>(G, D.l2l_child + D.l2l_off[l], n, C->L2L64, ndp, C->loc64, st));
+    }
+    if (tm) CU(cudaEventRecord(C->ev[4], st));
+    CU(launch_p2p_l2p_f64(G, L, C->W64, nsp, ntp, ndp, C->loc64, C->phi, st));
+  } else {
+    CU(launch_weights<float>(G, L.src_cls, nsp, C->dens[kind], nsel, ndens, ndp, C->W32, st));
+    CU(cudaMemsetAsync(C->mom32, 0, nexp * sizeof(float), st));
+    CU(cudaMemsetAsync(C->loc32, 0, nexp * sizeof(float), st));
+    if (tm) CU(cudaEventRecord(C->ev[1], st));
+    CU(launch_p2m<float>(G, L, C->W32, nsp, ndp, C->mom32, st));
+    for (int l = C->nlevels - 1; l >= 0; --l) {
+      const int n = D.m2m_off[l + 1] - D.m2m_off[l];
+      CU(launch_m2m<float>(G, D.m2m_parent + D.m2m_off[l], n, C->M2M32, ndp, C->mom32, st));
+    }
+    if (tm) CU(cudaEventRecord(C->ev[2], st));
+    if (tc) CU(launch_m2l_tc(G, L, C->tc, ndp, C->mom32, C->loc32, st));
+    else CU(launch_m2l_simt<float>(G, L, C->T32, G.tri_k, ndp, C->mom32, C->loc32, st));
+    if (tm) CU(cudaEventRecord(C->ev[3], st));
+    for (int l = 3; l < C->nlevels; ++l) {
+      const int n = D.l2l_off[l + 1] - D.l2l_off[l];
+      CU(launch_l2l<float>(G, D.l2l_child + D.l2l_off[l], n, C->L2L32, ndp, C->loc32, st));
+    }
+    if (tm) CU(cudaEventRecord(C->ev[4], st));
+    CU(launch_p2p_l2p_f32(G, L, C->W32, nsp, ntp, ndp, C->loc32, C->phi, st));
+  }
+  if (tm) CU(cudaEventRecord(C->ev[5], st));
+  CU(launch_elem_sum(G, L, C->phi, ntp, C->dens[kind], ndens, outd, st));
+  if (tm) CU(cudaEventRecord(C->ev[6], st));
+  if (!out_is_device) {
+    CU(cudaMemcpyAsync(out, C->out_dev, (size_t)ndens * L.ntgt_el * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+  }
+  if (tm) {
+    CU(cudaEventSynchronize(C->ev[6]));
+    for (int i = 0; i < 6; ++i) CU(cudaEventElapsedTime(&C->stage_ms[i], C->ev[i], C->ev[i + 1]));
+  }
+  return BCFMM_OK;
+}
+
+extern "C" int bcfmm_eval_vtv(bcfmm_ctx* C, double* out, int32_t d) { return eval_impl(C, 0, out, d); }
+extern "C" int bcfmm_eval_vtb(bcfmm_ctx* C, double* out, int32_t d) { return eval_impl(C, 1, out, d); }
+extern "C" int bcfmm_eval_btv(bcfmm_ctx* C, double* out, int32_t d) { return eval_impl(C, 2, out, d); }
+
+extern "C" int bcfmm_stats(const bcfmm_ctx* C, char* json, size_t cap) {
+  if (!C || !json) return fail(BCFMM_ERR_ARG, "stats: null argument");
+  std::string s = "{";
+  auto kv = [&](const char* k, double v, bool last = false) {
+    char b[96];
+    snprintf(b, sizeof b, "\"%s\": %.17g%s", k, v, last ? "" : ", ");
+    s += b;
+  };
+  kv("ntet", (double)C->ntet); kv("ntri", (double)C->ntri);
+  kv("npts_tet", (double)C->npts[0]); kv("npts_tri", (double)C->npts[1]);
+  kv("p", C->prm.p); kv("np", C->np); kv("leaf_size", C->prm.leaf_size); kv("precision", C->prm.precision);
+  kv("nbox", C->nbox); kv("nleaf", C->nleaf); kv("nlevels", C->nlevels);
+  kv("setup_s", C->sec_setup); kv("tree_s", C->sec_tree); kv("lists_s", C->sec_lists);
+  kv("near_search_s", C->sec_near_host); kv("near_rule_s", C->sec_near_dev);
+  const char* names[3] = {"vtv", "vtb", "btv"};
+  for (int t = 0; t < 3; ++t) {
+    char b[400];
+    snprintf(b, sizeof b,
+             "\"%s\": {\"p2p_pairs\": %lld, \"near_boxes\": %lld, \"m2l_pairs\": %lld, \"near_pairs\": %lld, "
+             "\"p2p_leaves\": %d, \"m2l_targets\": %d, \"p2m_leaves\": %d}, ",
+             names[t], (long long)C->task[t].p2p_pairs, (long long)C->task[t].near_boxes,
+             (long long)C->task[t].m2l_pairs, (long long)C->task[t].nnz, C->task[t].L.n_p2p, C->task[t].L.n_m2l,
+             C->task[t].L.n_p2m);
+    s += b;
+  }
+  s += "\"stage_ms\": [";
+  for (int i = 0; i < 6; ++i) { char b[32]; snprintf(b, sizeof b, "%.6g%s", C->stage_ms[i], i < 5 ? ", " : ""); s += b; }
+  s += "], \"leaves_per_level\": [";
+  for (size_t i = 0; i < C->leaves_per_level.size(); ++i) s += std::to_string(C->leaves_per_level[i]) + (i + 1 < C->leaves_per_level.size() ? ", " : "");
+  s += "], \"boxes_per_level\": [";
+  for (size_t i = 0; i < C->boxes_per_level.size(); ++i) s += std::to_string(C->boxes_per_level[i]) + (i + 1 < C->boxes_per_level.size() ? ", " : "");
+  s += "]}";
+  if (s.size() + 1 > cap) return fail(BCFMM_ERR_ARG, "stats: buffer too small, need " + std::to_string(s.size() + 1));
+  std::memcpy(json, s.c_str(), s.size() + 1);
+  return BCFMM_OK;
+}
+
+extern "C" void bcfmm_destroy(bcfmm_ctx* C) {
+  if (!C) return;
+  cudaStreamSynchronize(C->st);
+  if (C->ev_ok) for (auto& ev : C->ev) cudaEventDestroy(ev);
+  m2l_tc_free_tables(&C->tc);
+  C->mem.free_all();
+  delete C;
+}

@@ -1,0 +1,94 @@
+// Internal declarations of the bcfmm library (not part of the C ABI).
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace bcfmm {
+
+constexpr double kFourPi = 12.566370614359172953850573533118;
+constexpr int kMaxLevel = 18;
+constexpr int kMaxP = 12;
+constexpr int kNumOffsets = 343;   // o in [-3,3]^3, code = (ox+3) + 7 (oy+3) + 49 (oz+3)
+
+inline int nterms(int p) { return (p + 1) * (p + 2) * (p + 3) / 6; }
+
+// Multi-indices of total degree <= P: by degree, then (a desc, b desc).
+struct MultiIndex {
+  int P = 0, n = 0;
+  std::vector<int> a, b, c;
+  std::vector<int> lut;              // (P+1)^3
+  void init(int P_);
+  int at(int i, int j, int k) const {
+    if (i < 0 || j < 0 || k < 0 || i + j + k > P) return -1;
+    return lut[(i * (P + 1) + j) * (P + 1) + k];
+  }
+};
+
+// Box of the adaptive octree.  Levels are stored contiguously (BFS order).
+struct HostBox {
+  int level;
+  int64_t ijk[3];
+  int parent;
+  int child0, nchild;
+  int octant;                        // position in the parent (bit0 x, bit1 y, bit2 z)
+  int pt0[2], pt1[2];                // point ranges of class 0 (tet points) / 1 (tri points)
+  double c[3], s;
+};
+
+// Per task (VtV, VtB, BtV) lists, host side.
+struct HostTask {
+  int src_cls = 0, tgt_cls = 0;
+  // P2P: target leaves and their extended neighbour list N* as box ids
+  std::vector<int> p2p_leaf, near_off, near_box;
+  // M2L: target boxes (level >= 2 with target points) and interaction lists
+  std::vector<int> m2l_tgt, vl_off, vl_src;
+  std::vector<uint16_t> vl_code;
+  // upward / downward restricted to boxes with source / target points
+  std::vector<int> p2m_leaf;                       // leaves with source points
+  std::vector<std::vector<int>> m2m_parent;        // per level: non-leaf boxes with source points
+  std::vector<std::vector<int>> l2l_child;         // per level: boxes (level>=3) with target points
+  std::vector<int> l2p_leaf;                       // leaves (level >= 2) with target points
+  // near element pairs, CSR over target elements
+  std::vector<int64_t> cor_off;
+  std::vector<int32_t> cor_col;
+};
+
+struct HostSetup {
+  int64_t ntet = 0, ntri = 0;
+  std::vector<double> tet_v, tri_v;                // [ntet][4][3], [ntri][3][3]
+  std::vector<double> tet_vol, tri_area;
+  // quadrature points (original order): class 0 tet points 4/tet, class 1 tri points 3/tri
+  std::vector<double> qp[2], qw[2];
+  // tree
+  double lo[3], R0;
+  std::vector<HostBox> box;
+  std::vector<int> lvl_off;                        // box index range per level
+  int nlevels = 0;
+  std::vector<int> perm[2];                        // sorted position -> original point index
+  std::vector<int> leaf_of[2];                     // sorted position -> leaf box
+  HostTask task[3];
+  double seconds_tree = 0, seconds_lists = 0, seconds_near = 0;
+};
+
+// Validates the mesh, computes element geometry and quadrature points.
+// Returns "" on success, else an error message; *mesh_err set when the
+// failure is a degenerate element.
+std::string setup_mesh(HostSetup& H, const double* verts, int64_t nvert, const int32_t* tets,
+                       int64_t ntet, const int32_t* tris, int64_t ntri, bool* mesh_err);
+void build_tree(HostSetup& H, int leaf_size);
+void build_lists(HostSetup& H);
+void find_near_pairs(HostSetup& H, double eta_ns);
+
+// Gauss-Legendre nodes/weights on [0,1] (Newton iteration on P_n).
+void gauss_legendre01(int n, std::vector<double>& x, std::vector<double>& w);
+
+// Box-scaled translation tables (Sec. 3.3).
+//  M2L: T[code][a][b] for all 343 offset codes (zero for |o|_inf <= 1).
+//  M2M: for child octant q, m_parent[b] += sum_g M[q][b][g] m_child[g].
+//  L2L: for child octant q, l_child[a] += sum_b L[q][a][b] l_parent[b].
+void m2l_matrix_scaled(int p, const double o[3], double* T);
+void m2m_matrices(int p, std::vector<double>& M);
+void l2l_matrices(int p, std::vector<double>& L);
+
+}  // namespace bcfmm

@@ -1,0 +1,68 @@
+// Device-side declarations shared by the bcfmm translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace bcfmm {
+
+// Geometry and lists the evaluation kernels read (device pointers).
+struct DevGeom {
+  int np;                        // nterms(p)
+  int p;
+  int nbox;
+  const int* mi;                 // packed multi-indices a | b << 8 | c << 16, degree-major
+  const int* tri_k;              // per row alpha: nterms(p - |alpha|)
+  const double4_32a* box_cs;         // centre xyz, side s
+  const int* box_child0;
+  const int* box_nchild;
+  const int* box_octant;
+  const int* box_parent;
+  const int2* box_rng[2];        // point range per class
+  const double4_32a* pt64[2];        // sorted points: x, y, z, quadrature weight
+  const float4* pthi[2];         // float hi parts (x, y, z, weight)
+  const float4* ptlo[2];         // float lo parts (x - hi, ...)
+  const int* pt_elem[2];         // sorted point -> element
+};
+
+struct DevTaskLists {
+  int n_p2p; const int* p2p_leaf; const int* near_off; const int* near_box;
+  int n_m2l; const int* m2l_tgt; const int* vl_off; const int* vl_src; const uint16_t* vl_code;
+  int n_p2m; const int* p2m_leaf;
+  int n_l2p; const int* l2p_leaf;
+  int64_t ntgt_el, nsrc_el;
+  const int64_t* cor_off; const int* cor_col; const double* cor_val;
+  const int* elem_pts;           // [ntgt_el][4] sorted positions of the element's points (-1 pad)
+  int nq_tgt;                    // 4 (tets) or 3 (triangles)
+  int src_cls, tgt_cls;
+};
+
+// launchers (return cudaGetLastError())
+template <typename T>
+cudaError_t launch_weights(const DevGeom& G, int cls, int64_t n, const double* dens, int64_t nel, int ndens,
+                           int ndp, T* W, cudaStream_t st);
+template <typename T>
+cudaError_t launch_p2m(const DevGeom& G, const DevTaskLists& L, const T* W, int64_t nsrc_pts, int ndp,
+                       T* mom, cudaStream_t st);
+template <typename T>
+cudaError_t launch_m2m(const DevGeom& G, const int* parents, int n, const T* M2M, int ndp, T* mom, cudaStream_t st);
+template <typename T>
+cudaError_t launch_m2l_simt(const DevGeom& G, const DevTaskLists& L, const T* Tt, const int* tri_k,
+                            int ndp, const T* mom, T* loc, cudaStream_t st);
+template <typename T>
+cudaError_t launch_l2l(const DevGeom& G, const int* children, int n, const T* L2L, int ndp, T* loc, cudaStream_t st);
+cudaError_t launch_p2p_l2p_f32(const DevGeom& G, const DevTaskLists& L, const float* W, int64_t nsrc_pts,
+                               int64_t ntgt_pts, int ndp, const float* loc, double* phi, cudaStream_t st);
+cudaError_t launch_p2p_l2p_f64(const DevGeom& G, const DevTaskLists& L, const double* W, int64_t nsrc_pts,
+                               int64_t ntgt_pts, int ndp, const double* loc, double* phi, cudaStream_t st);
+cudaError_t launch_elem_sum(const DevGeom& G, const DevTaskLists& L, const double* phi, int64_t ntgt_pts,
+                            const double* dens_src, int ndens, double* out, cudaStream_t st);
+
+// setup: near-rule corrections C_ts = N_ts - Q_ts (FP64)
+cudaError_t launch_near_rule(int task, int64_t nnz, const int* row, const int* col,
+                             const double* tgt_v, const double* src_v,
+                             const double* tgt_qp, const double* tgt_qw,
+                             const double* src_qp, const double* src_qw,
+                             const double* glx, const double* glw, int n, int k,
+                             double* cor_val, cudaStream_t st);
+
+}  // namespace bcfmm

@@ -1,0 +1,460 @@
+// Evaluation kernels of the boundary-concentrated FMM (Sec. 3.3, Algorithms
+// 1-3): source weights, moments (P2M), upward pass (M2M), interaction phase
+// on CUDA cores (M2L), downward pass (L2L), evaluation fused with the near
+// field (L2P + P2P over the extended neighbour list N*), and the Galerkin
+// element sums plus near-rule corrections.
+//
+// Expansions are box-scaled: moments m^b = sum_j W_j ((y_j - c)/s)^b, locals
+// phi(x) = sum_a l^a ((x - c)/s)^a, so one M2L table per integer offset
+// serves every level (the 1/s factor is applied here).
+#include <cstdio>
+
+#include "kernels.cuh"
+
+namespace bcfmm {
+
+constexpr double kInv4Pi = 0.079577471545947667884441881686257;
+
+// ------------------------------------------------------------ weights
+// W[d][j] = w_j * dens[d][elem(j)] (d < ndens), zero for ndens <= d < ndp.
+template <typename T>
+__global__ void k_weights(const double4_32a* __restrict__ pt, const int* __restrict__ elem, int64_t n,
+                          const double* __restrict__ dens, int64_t nel, int ndens, int ndp, T* __restrict__ W) {
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double w = pt[j].w;
+  int e = elem[j];
+  for (int d = 0; d < ndp; ++d) W[(int64_t)d * n + j] = (T)(d < ndens ? w * dens[(int64_t)d * nel + e] : 0.0);
+}
+
+template <typename T>
+cudaError_t launch_weights(const DevGeom& G, int cls, int64_t n, const double* dens, int64_t nel, int ndens,
+                           int ndp, T* W, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_weights<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(G.pt64[cls], G.pt_elem[cls], n, dens, nel, ndens, ndp, W);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- P2M
+// One CTA per leaf; thread per coefficient; powers of the scaled offsets
+// staged in shared memory for a chunk of 64 points.
+template <typename T>
+__global__ void k_p2m(DevGeom G, const int* __restrict__ leaves, int cls, const T* __restrict__ W, int64_t nsp,
+                      int ndp, T* __restrict__ mom) {
+  extern __shared__ unsigned char smraw[];
+  const int P = G.p, np = G.np;
+  T* pw = reinterpret_cast<T*>(smraw);               // [3][P+1][64]
+  T* ws = pw + 3 * (P + 1) * 64;                     // [ndp][64]
+  const int leaf = leaves[blockIdx.x];
+  const double4_32a cs = G.box_cs[leaf];
+  const int2 r = G.box_rng[cls][leaf];
+  const double inv_s = 1.0 / cs.w;
+  for (int j0 = r.x; j0 < r.y; j0 += 64) {
+    const int m = min(64, r.y - j0);
+    __syncthreads();
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+      const double4_32a y = G.pt64[cls][j0 + j];
+      const T d[3] = {(T)((y.x - cs.x) * inv_s), (T)((y.y - cs.y) * inv_s), (T)((y.z - cs.z) * inv_s)};
+      for (int ax = 0; ax < 3; ++ax) {
+        T v = (T)1;
+        for (int k = 0; k <= P; ++k) { pw[(ax * (P + 1) + k) * 64 + j] = v; v *= d[ax]; }
+      }
+      for (int dd = 0; dd < ndp; ++dd) ws[dd * 64 + j] = W[(int64_t)dd * nsp + j0 + j];
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < np; q += blockDim.x) {
+      const int mi = G.mi[q];
+      const int a = mi & 255, b = (mi >> 8) & 255, c = (mi >> 16) & 255;
+      const T* px = pw + (0 * (P + 1) + a) * 64;
+      const T* py = pw + (1 * (P + 1) + b) * 64;
+      const T* pz = pw + (2 * (P + 1) + c) * 64;
+      for (int dd = 0; dd < ndp; ++dd) {
+        T acc = 0;
+        for (int j = 0; j < m; ++j) acc += ws[dd * 64 + j] * px[j] * py[j] * pz[j];
+        mom[((int64_t)leaf * ndp + dd) * np + q] += acc;
+      }
+    }
+  }
+}
+
+template <typename T>
+cudaError_t launch_p2m(const DevGeom& G, const DevTaskLists& L, const T* W, int64_t nsrc_pts, int ndp,
+                       T* mom, cudaStream_t st) {
+  if (L.n_p2m == 0) return cudaSuccess;
+  size_t sm = sizeof(T) * (3 * (G.p + 1) * 64 + ndp * 64);
+  k_p2m<T><<<L.n_p2m, 128, sm, st>>>(G, L.p2m_leaf, L.src_cls, W, nsrc_pts, ndp, mom);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- M2M
+// m_parent[b] = sum_children sum_g M[octant][b][g] m_child[g]
+template <typename T>
+__global__ void k_m2m(DevGeom G, const int* __restrict__ parents, const T* __restrict__ M2M, int ndp,
+                      T* __restrict__ mom) {
+  extern __shared__ unsigned char smraw[];
+  T* mc = reinterpret_cast<T*>(smraw);               // [8][np]
+  const int np = G.np;
+  const int P = parents[blockIdx.x];
+  const int c0 = G.box_child0[P], nc = G.box_nchild[P];
+  for (int d = 0; d < ndp; ++d) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < nc * np; i += blockDim.x) {
+      int c = i / np, q = i % np;
+      mc[i] = mom[((int64_t)(c0 + c) * ndp + d) * np + q];
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < np; b += blockDim.x) {
+      T acc = 0;
+      for (int c = 0; c < nc; ++c) {
+        const T* Mr = M2M + ((int64_t)G.box_octant[c0 + c] * np + b) * np;
+        for (int g = 0; g <= b; ++g) acc += Mr[g] * mc[c * np + g];   // g <= b: lower degree first
+      }
+      mom[((int64_t)P * ndp + d) * np + b] = acc;
+    }
+  }
+}
+
+template <typename T>
+cudaError_t launch_m2m(const DevGeom& G, const int* parents, int n, const T* M2M, int ndp, T* mom, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_m2m<T><<<n, 128, sizeof(T) * 8 * G.np, st>>>(G, parents, M2M, ndp, mom);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- M2L
+// One CTA per target box, thread per row alpha of the local expansion.
+// Tt[code][b][a] is the transposed table (coalesced over alpha); row alpha
+// needs only b < tri_k[alpha] = nterms(p - |alpha|).
+template <typename T, int ND>
+__global__ void k_m2l_simt(DevGeom G, DevTaskLists L, const T* __restrict__ Tt, int ndp,
+                           const T* __restrict__ mom, T* __restrict__ loc) {
+  extern __shared__ unsigned char smraw[];
+  T* ms = reinterpret_cast<T*>(smraw);               // [ND][np]
+  const int np = G.np;
+  const int tb = L.m2l_tgt[blockIdx.x];
+  const int a = threadIdx.x;
+  const int K = (a < np) ? G.tri_k[a] : 0;
+  T acc[ND];
+#pragma unroll
+  for (int d = 0; d < ND; ++d) acc[d] = 0;
+  const int e0 = L.vl_off[blockIdx.x], e1 = L.vl_off[blockIdx.x + 1];
+  for (int e = e0; e < e1; ++e) {
+    const int sb = L.vl_src[e];
+    const T* Tc = Tt + (int64_t)L.vl_code[e] * np * np;
+    __syncthreads();
+    for (int i = threadIdx.x; i < ND * np; i += blockDim.x) ms[i] = mom[(int64_t)sb * ndp * np + i];
+    __syncthreads();
+    if (a < np) {
+      for (int b = 0; b < K; ++b) {
+        const T t = Tc[(int64_t)b * np + a];
+#pragma unroll
+        for (int d = 0; d < ND; ++d) acc[d] += t * ms[d * np + b];
+      }
+    }
+  }
+  if (a < np) {
+    const T inv_s = (T)(1.0 / G.box_cs[tb].w);
+#pragma unroll
+    for (int d = 0; d < ND; ++d) loc[((int64_t)tb * ndp + d) * np + a] = acc[d] * inv_s;
+  }
+}
+
+template <typename T>
+cudaError_t launch_m2l_simt(const DevGeom& G, const DevTaskLists& L, const T* Tt, const int* /*tri_k*/,
+                            int ndp, const T* mom, T* loc, cudaStream_t st) {
+  if (L.n_m2l == 0) return cudaSuccess;
+  int threads = ((G.np + 31) / 32) * 32;
+  size_t sm = sizeof(T) * ndp * G.np;
+  switch (ndp) {
+    case 1: k_m2l_simt<T, 1><<<L.n_m2l, threads, sm, st>>>(G, L, Tt, ndp, mom, loc); break;
+    case 2: k_m2l_simt<T, 2><<<L.n_m2l, threads, sm, st>>>(G, L, Tt, ndp, mom, loc); break;
+    case 4: k_m2l_simt<T, 4><<<L.n_m2l, threads, sm, st>>>(G, L, Tt, ndp, mom, loc); break;
+    case 8: k_m2l_simt<T, 8><<<L.n_m2l, threads, sm, st>>>(G, L, Tt, ndp, mom, loc); break;
+    case 16: k_m2l_simt<T, 16><<<L.n_m2l, threads, sm, st>>>(G, L, Tt, ndp, mom, loc); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- L2L
+// l_child[a] += sum_{b >= a} L[octant][a][b] l_parent[b]
+template <typename T>
+__global__ void k_l2l(DevGeom G, const int* __restrict__ children, const T* __restrict__ L2L, int ndp,
+                      T* __restrict__ loc) {
+  extern __shared__ unsigned char smraw[];
+  T* lp = reinterpret_cast<T*>(smraw);               // [np]
+  const int np = G.np;
+  const int C = children[blockIdx.x];
+  const int P = G.box_parent[C];
+  const T* Lm = L2L + (int64_t)G.box_octant[C] * np * np;
+  for (int d = 0; d < ndp; ++d) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < np; i += blockDim.x) lp[i] = loc[((int64_t)P * ndp + d) * np + i];
+    __syncthreads();
+    for (int a = threadIdx.x; a < np; a += blockDim.x) {
+      T acc = 0;
+      const T* Lr = Lm + (int64_t)a * np;
+      for (int b = a; b < np; ++b) acc += Lr[b] * lp[b];
+      loc[((int64_t)C * ndp + d) * np + a] += acc;
+    }
+  }
+}
+
+template <typename T>
+cudaError_t launch_l2l(const DevGeom& G, const int* children, int n, const T* L2L, int ndp, T* loc, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_l2l<T><<<n, 128, sizeof(T) * G.np, st>>>(G, children, L2L, ndp, loc);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------ evaluation + near field
+// One CTA (128 threads) per target leaf.  Targets are padded to TP in
+// {32, 64, 128}; the 128/TP thread groups split each source tile and are
+// reduced at the end.  Source tiles are staged in shared memory, translated
+// to the target leaf's frame with double-float (hi + lo) arithmetic so that
+// FP32 differences keep full relative accuracy.  The self point (r == 0) is
+// skipped.  FP32 partial sums are folded into FP64 once per source box.
+constexpr int kTile = 256;
+
+__device__ __forceinline__ void split_df(double v, float& hi, float& lo) {
+  hi = (float)v;
+  lo = (float)(v - (double)hi);
+}
+
+template <int ND>
+__global__ void __launch_bounds__(128) k_p2p_l2p_f32(DevGeom G, DevTaskLists L, const float* __restrict__ W,
+                                                     int64_t nsp, int64_t ntp, int ndp,
+                                                     const float* __restrict__ loc, double* __restrict__ phi) {
+  __shared__ float sx[kTile], sy[kTile], sz[kTile];
+  __shared__ float sw[ND][kTile];
+  __shared__ double red[ND][128];
+  const int leaf = L.p2p_leaf[blockIdx.x];
+  const int sc = L.src_cls, tc = L.tgt_cls;
+  const double4_32a cs = G.box_cs[leaf];
+  float chx, clx, chy, cly, chz, clz;
+  split_df(cs.x, chx, clx); split_df(cs.y, chy, cly); split_df(cs.z, chz, clz);
+  const int2 tr = G.box_rng[tc][leaf];
+  const int nt = tr.y - tr.x;
+  const int TP = nt <= 32 ? 32 : (nt <= 64 ? 64 : 128);
+  const int NG = 128 / TP;
+  const int ti = threadIdx.x % TP, gi = threadIdx.x / TP;
+  const bool active = ti < nt;
+  float xt = 0.f, yt = 0.f, zt = 0.f;
+  if (active) {
+    const float4 h = G.pthi[tc][tr.x + ti], l = G.ptlo[tc][tr.x + ti];
+    xt = (h.x - chx) + (l.x - clx);
+    yt = (h.y - chy) + (l.y - cly);
+    zt = (h.z - chz) + (l.z - clz);
+  }
+  double accd[ND];
+  float acc[ND];
+#pragma unroll
+  for (int d = 0; d < ND; ++d) { accd[d] = 0.0; acc[d] = 0.f; }
+  const int n0 = L.near_off[blockIdx.x], n1 = L.near_off[blockIdx.x + 1];
+  for (int nb = n0; nb < n1; ++nb) {
+    const int2 sr = G.box_rng[sc][L.near_box[nb]];
+    for (int j0 = sr.x; j0 < sr.y; j0 += kTile) {
+      const int m = min(kTile, sr.y - j0);
+      __syncthreads();
+      for (int j = threadIdx.x; j < m; j += 128) {
+        const float4 h = G.pthi[sc][j0 + j], l = G.ptlo[sc][j0 + j];
+        sx[j] = (h.x - chx) + (l.x - clx);
+        sy[j] = (h.y - chy) + (l.y - cly);
+        sz[j] = (h.z - chz) + (l.z - clz);
+#pragma unroll
+        for (int d = 0; d < ND; ++d) sw[d][j] = W[(int64_t)d * nsp + j0 + j];
+      }
+      __syncthreads();
+      if (active) {
+#pragma unroll 4
+        for (int j = gi; j < m; j += NG) {
+          const float dx = xt - sx[j], dy = yt - sy[j], dz = zt - sz[j];
+          const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+          const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+#pragma unroll
+          for (int d = 0; d < ND; ++d) acc[d] = fmaf(sw[d][j], rinv, acc[d]);
+        }
+      }
+    }
+#pragma unroll
+    for (int d = 0; d < ND; ++d) { accd[d] += (double)acc[d]; acc[d] = 0.f; }
+  }
+  // reduce the NG source groups
+#pragma unroll
+  for (int d = 0; d < ND; ++d) red[d][threadIdx.x] = accd[d];
+  __syncthreads();
+  if (gi == 0 && active) {
+    double far[ND];
+#pragma unroll
+    for (int d = 0; d < ND; ++d) far[d] = 0.0;
+    // L2P: phi_far(x) = sum_a l^a xhat^a, xhat = (x - c)/s (locals of boxes
+    // without an interaction list are zero)
+    if (loc != nullptr) {
+      const float inv_s = (float)(1.0 / cs.w);
+      const float xs = xt * inv_s, ys = yt * inv_s, zs = zt * inv_s;
+      float px[16], py[16], pz[16];
+      px[0] = py[0] = pz[0] = 1.f;
+      for (int k = 1; k <= G.p; ++k) { px[k] = px[k - 1] * xs; py[k] = py[k - 1] * ys; pz[k] = pz[k - 1] * zs; }
+      const float* lb = loc + (int64_t)leaf * ndp * G.np;
+      for (int q = 0; q < G.np; ++q) {
+        const int mi = G.mi[q];
+        const float mono = px[mi & 255] * py[(mi >> 8) & 255] * pz[(mi >> 16) & 255];
+#pragma unroll
+        for (int d = 0; d < ND; ++d) far[d] += (double)(lb[d * G.np + q] * mono);
+      }
+    }
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+      double s = 0.0;
+      for (int g = 0; g < NG; ++g) s += red[d][g * TP + ti];
+      phi[(int64_t)d * ntp + tr.x + ti] = s * kInv4Pi + far[d];
+    }
+  }
+}
+
+template <int ND>
+__global__ void __launch_bounds__(128) k_p2p_l2p_f64(DevGeom G, DevTaskLists L, const double* __restrict__ W,
+                                                     int64_t nsp, int64_t ntp, int ndp,
+                                                     const double* __restrict__ loc, double* __restrict__ phi) {
+  __shared__ double sx[kTile / 2], sy[kTile / 2], sz[kTile / 2];
+  __shared__ double sw[ND][kTile / 2];
+  __shared__ double red[ND][128];
+  constexpr int TL = kTile / 2;
+  const int leaf = L.p2p_leaf[blockIdx.x];
+  const int sc = L.src_cls, tc = L.tgt_cls;
+  const double4_32a cs = G.box_cs[leaf];
+  const int2 tr = G.box_rng[tc][leaf];
+  const int nt = tr.y - tr.x;
+  const int TP = nt <= 32 ? 32 : (nt <= 64 ? 64 : 128);
+  const int NG = 128 / TP;
+  const int ti = threadIdx.x % TP, gi = threadIdx.x / TP;
+  const bool active = ti < nt;
+  double xt = 0, yt = 0, zt = 0;
+  if (active) {
+    const double4_32a x = G.pt64[tc][tr.x + ti];
+    xt = x.x; yt = x.y; zt = x.z;
+  }
+  double acc[ND];
+#pragma unroll
+  for (int d = 0; d < ND; ++d) acc[d] = 0.0;
+  const int n0 = L.near_off[blockIdx.x], n1 = L.near_off[blockIdx.x + 1];
+  for (int nb = n0; nb < n1; ++nb) {
+    const int2 sr = G.box_rng[sc][L.near_box[nb]];
+    for (int j0 = sr.x; j0 < sr.y; j0 += TL) {
+      const int m = min(TL, sr.y - j0);
+      __syncthreads();
+      for (int j = threadIdx.x; j < m; j += 128) {
+        const double4_32a y = G.pt64[sc][j0 + j];
+        sx[j] = y.x; sy[j] = y.y; sz[j] = y.z;
+#pragma unroll
+        for (int d = 0; d < ND; ++d) sw[d][j] = W[(int64_t)d * nsp + j0 + j];
+      }
+      __syncthreads();
+      if (active) {
+        for (int j = gi; j < m; j += NG) {
+          const double dx = xt - sx[j], dy = yt - sy[j], dz = zt - sz[j];
+          const double r2 = dx * dx + dy * dy + dz * dz;
+          const double rinv = r2 > 0.0 ? 1.0 / sqrt(r2) : 0.0;
+#pragma unroll
+          for (int d = 0; d < ND; ++d) acc[d] += sw[d][j] * rinv;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int d = 0; d < ND; ++d) red[d][threadIdx.x] = acc[d];
+  __syncthreads();
+  if (gi == 0 && active) {
+    double far[ND];
+#pragma unroll
+    for (int d = 0; d < ND; ++d) far[d] = 0.0;
+    if (loc != nullptr) {
+      const double inv_s = 1.0 / cs.w;
+      const double xs = (xt - cs.x) * inv_s, ys = (yt - cs.y) * inv_s, zs = (zt - cs.z) * inv_s;
+      double px[16], py[16], pz[16];
+      px[0] = py[0] = pz[0] = 1.0;
+      for (int k = 1; k <= G.p; ++k) { px[k] = px[k - 1] * xs; py[k] = py[k - 1] * ys; pz[k] = pz[k - 1] * zs; }
+      const double* lb = loc + (int64_t)leaf * ndp * G.np;
+      for (int q = 0; q < G.np; ++q) {
+        const int mi = G.mi[q];
+        const double mono = px[mi & 255] * py[(mi >> 8) & 255] * pz[(mi >> 16) & 255];
+#pragma unroll
+        for (int d = 0; d < ND; ++d) far[d] += lb[d * G.np + q] * mono;
+      }
+    }
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+      double s = 0.0;
+      for (int g = 0; g < NG; ++g) s += red[d][g * TP + ti];
+      phi[(int64_t)d * ntp + tr.x + ti] = s * kInv4Pi + far[d];
+    }
+  }
+}
+
+#define P2P_DISPATCH(KER, ...)                                               \
+  switch (ndp) {                                                             \
+    case 1: KER<1><<<L.n_p2p, 128, 0, st>>>(__VA_ARGS__); break;             \
+    case 2: KER<2><<<L.n_p2p, 128, 0, st>>>(__VA_ARGS__); break;             \
+    case 4: KER<4><<<L.n_p2p, 128, 0, st>>>(__VA_ARGS__); break;             \
+    case 8: KER<8><<<L.n_p2p, 128, 0, st>>>(__VA_ARGS__); break;             \
+    case 16: KER<16><<<L.n_p2p, 128, 0, st>>>(__VA_ARGS__); break;           \
+    default: return cudaErrorInvalidValue;                                   \
+  }
+
+cudaError_t launch_p2p_l2p_f32(const DevGeom& G, const DevTaskLists& L, const float* W, int64_t nsrc_pts,
+                               int64_t ntgt_pts, int ndp, const float* loc, double* phi, cudaStream_t st) {
+  if (L.n_p2p == 0) return cudaSuccess;
+  P2P_DISPATCH(k_p2p_l2p_f32, G, L, W, nsrc_pts, ntgt_pts, ndp, loc, phi);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_p2p_l2p_f64(const DevGeom& G, const DevTaskLists& L, const double* W, int64_t nsrc_pts,
+                               int64_t ntgt_pts, int ndp, const double* loc, double* phi, cudaStream_t st) {
+  if (L.n_p2p == 0) return cudaSuccess;
+  P2P_DISPATCH(k_p2p_l2p_f64, G, L, W, nsrc_pts, ntgt_pts, ndp, loc, phi);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------- Galerkin sums + corrections
+// One warp per target element: u[d][e] = sum_q w_q phi[d][pos_q]
+//                                      + sum_k C[k] dens[d][col[k]].
+__global__ void k_elem_sum(DevGeom G, DevTaskLists L, const double* __restrict__ phi, int64_t ntp,
+                           const double* __restrict__ dens, int ndens, double* __restrict__ out) {
+  const int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (e >= L.ntgt_el) return;
+  const int tc = L.tgt_cls;
+  for (int d = 0; d < ndens; ++d) {
+    double s = 0.0;
+    if (lane < L.nq_tgt) {
+      const int pos = L.elem_pts[e * 4 + lane];
+      s = G.pt64[tc][pos].w * phi[(int64_t)d * ntp + pos];
+    }
+    const int64_t k0 = L.cor_off[e], k1 = L.cor_off[e + 1];
+    for (int64_t k = k0 + lane; k < k1; k += 32) s += L.cor_val[k] * dens[(int64_t)d * L.nsrc_el + L.cor_col[k]];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[(int64_t)d * L.ntgt_el + e] = s;
+  }
+}
+
+cudaError_t launch_elem_sum(const DevGeom& G, const DevTaskLists& L, const double* phi, int64_t ntgt_pts,
+                            const double* dens_src, int ndens, double* out, cudaStream_t st) {
+  if (L.ntgt_el == 0) return cudaSuccess;
+  const int64_t threads = L.ntgt_el * 32;
+  k_elem_sum<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(G, L, phi, ntgt_pts, dens_src, ndens, out);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_weights<float>(const DevGeom&, int, int64_t, const double*, int64_t, int, int, float*, cudaStream_t);
+template cudaError_t launch_weights<double>(const DevGeom&, int, int64_t, const double*, int64_t, int, int, double*, cudaStream_t);
+template cudaError_t launch_p2m<float>(const DevGeom&, const DevTaskLists&, const float*, int64_t, int, float*, cudaStream_t);
+template cudaError_t launch_p2m<double>(const DevGeom&, const DevTaskLists&, const double*, int64_t, int, double*, cudaStream_t);
+template cudaError_t launch_m2m<float>(const DevGeom&, const int*, int, const float*, int, float*, cudaStream_t);
+template cudaError_t launch_m2m<double>(const DevGeom&, const int*, int, const double*, int, double*, cudaStream_t);
+template cudaError_t launch_m2l_simt<float>(const DevGeom&, const DevTaskLists&, const float*, const int*, int, const float*, float*, cudaStream_t);
+template cudaError_t launch_m2l_simt<double>(const DevGeom&, const DevTaskLists&, const double*, const int*, int, const double*, double*, cudaStream_t);
+template cudaError_t launch_l2l<float>(const DevGeom&, const int*, int, const float*, int, float*, cudaStream_t);
+template cudaError_t launch_l2l<double>(const DevGeom&, const int*, int, const double*, int, double*, cudaStream_t);
+
+}  // namespace bcfmm

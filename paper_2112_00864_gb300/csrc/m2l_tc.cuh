@@ -1,0 +1,25 @@
+// Tensor-core (tcgen05) M2L of the boundary-concentrated FMM.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "kernels.cuh"
+
+namespace bcfmm {
+
+constexpr int kTcMaxP = 8;
+
+// Device tables of the tensor-core M2L (BF16 split parts of the box-scaled
+// translation matrices, one per offset code).
+struct M2LTensorTables {
+  void* tab = nullptr;   // bf16 parts, layout private to m2l_tc.cu
+  int p = 0, nsplit = 0;
+};
+
+bool m2l_tc_supported(int p);
+cudaError_t m2l_tc_prepare_tables(int p, const double* T /*[343][np][np]*/, int nsplit, M2LTensorTables* out,
+                                  cudaStream_t st);
+cudaError_t launch_m2l_tc(const DevGeom& G, const DevTaskLists& L, const M2LTensorTables& tab, int ndp,
+                          const float* mom, float* loc, cudaStream_t st);
+void m2l_tc_free_tables(M2LTensorTables* t);
+
+}  // namespace bcfmm

@@ -1,0 +1,513 @@
+// Host-side setup of the bcfmm library: mesh checks, element quadrature,
+// the adaptive octree, per-task interaction / extended-neighbour lists, the
+// near element-pair search and the translation tables.  FP64 throughout.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <unordered_map>
+
+#include "internal.h"
+
+namespace bcfmm {
+
+static double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+void MultiIndex::init(int P_) {
+  P = P_;
+  n = nterms(P);
+  a.resize(n); b.resize(n); c.resize(n);
+  lut.assign((P + 1) * (P + 1) * (P + 1), -1);
+  int q = 0;
+  for (int d = 0; d <= P; ++d)
+    for (int i = d; i >= 0; --i)
+      for (int j = d - i; j >= 0; --j) {
+        int k = d - i - j;
+        a[q] = i; b[q] = j; c[q] = k;
+        lut[(i * (P + 1) + j) * (P + 1) + k] = q;
+        ++q;
+      }
+}
+
+// ---------------------------------------------------------------- geometry
+static inline void vsub(const double* a, const double* b, double* o) { o[0] = a[0] - b[0]; o[1] = a[1] - b[1]; o[2] = a[2] - b[2]; }
+static inline double vdot(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+static inline void vcross(const double* a, const double* b, double* o) {
+  o[0] = a[1] * b[2] - a[2] * b[1]; o[1] = a[2] * b[0] - a[0] * b[2]; o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+std::string setup_mesh(HostSetup& H, const double* verts, int64_t nvert, const int32_t* tets,
+                       int64_t ntet, const int32_t* tris, int64_t ntri, bool* mesh_err) {
+  *mesh_err = false;
+  H.ntet = ntet; H.ntri = ntri;
+  H.tet_v.resize(12 * ntet); H.tri_v.resize(9 * ntri);
+  H.tet_vol.resize(ntet); H.tri_area.resize(ntri);
+  for (int64_t i = 0; i < 3 * nvert; ++i)
+    if (!std::isfinite(verts[i])) { *mesh_err = true; return "vertex " + std::to_string(i / 3) + " is not finite"; }
+  for (int64_t t = 0; t < ntet; ++t) {
+    for (int q = 0; q < 4; ++q) {
+      int32_t v = tets[4 * t + q];
+      if (v < 0 || v >= nvert) return "tet " + std::to_string(t) + " has vertex id out of range";
+      std::memcpy(&H.tet_v[12 * t + 3 * q], verts + 3 * (int64_t)v, 3 * sizeof(double));
+    }
+    const double* v = &H.tet_v[12 * t];
+    double a[3], b[3], c[3], n[3];
+    vsub(v + 3, v, a); vsub(v + 6, v, b); vsub(v + 9, v, c); vcross(a, b, n);
+    H.tet_vol[t] = std::fabs(vdot(n, c)) / 6.0;
+    if (!(H.tet_vol[t] > 0)) { *mesh_err = true; return "tet " + std::to_string(t) + " has zero volume"; }
+  }
+  for (int64_t t = 0; t < ntri; ++t) {
+    for (int q = 0; q < 3; ++q) {
+      int32_t v = tris[3 * t + q];
+      if (v < 0 || v >= nvert) return "triangle " + std::to_string(t) + " has vertex id out of range";
+      std::memcpy(&H.tri_v[9 * t + 3 * q], verts + 3 * (int64_t)v, 3 * sizeof(double));
+    }
+    const double* v = &H.tri_v[9 * t];
+    double a[3], b[3], n[3];
+    vsub(v + 3, v, a); vsub(v + 6, v, b); vcross(a, b, n);
+    H.tri_area[t] = 0.5 * std::sqrt(vdot(n, n));
+    if (!(H.tri_area[t] > 0)) { *mesh_err = true; return "triangle " + std::to_string(t) + " has zero area"; }
+  }
+  // element quadrature: tet degree-2 4-point rule, triangle interior 3-point rule
+  const double ta = (5.0 + 3.0 * std::sqrt(5.0)) / 20.0, tb = (5.0 - std::sqrt(5.0)) / 20.0;
+  H.qp[0].resize(12 * ntet); H.qw[0].resize(4 * ntet);
+  for (int64_t t = 0; t < ntet; ++t) {
+    const double* v = &H.tet_v[12 * t];
+    for (int q = 0; q < 4; ++q) {
+      for (int k = 0; k < 3; ++k) {
+        double s = 0.0;
+        for (int i = 0; i < 4; ++i) s += (i == q ? ta : tb) * v[3 * i + k];
+        H.qp[0][3 * (4 * t + q) + k] = s;
+      }
+      H.qw[0][4 * t + q] = 0.25 * H.tet_vol[t];
+    }
+  }
+  H.qp[1].resize(9 * ntri); H.qw[1].resize(3 * ntri);
+  for (int64_t t = 0; t < ntri; ++t) {
+    const double* v = &H.tri_v[9 * t];
+    for (int q = 0; q < 3; ++q) {
+      for (int k = 0; k < 3; ++k) {
+        double s = 0.0;
+        for (int i = 0; i < 3; ++i) s += (i == q ? 2.0 / 3.0 : 1.0 / 6.0) * v[3 * i + k];
+        H.qp[1][3 * (3 * t + q) + k] = s;
+      }
+      H.qw[1][3 * t + q] = H.tri_area[t] / 3.0;
+    }
+  }
+  return "";
+}
+
+// -------------------------------------------------------------------- tree
+// Root: bounding box of all element vertices, half width R0 = largest half
+// extent; level-l box (i,j,k): side s = 2 R0 / 2^l, centre lo + (i+1/2) s.
+// A box holding more than leaf_size points (both classes) is split; a point
+// goes to the upper child along every axis where it is >= the box centre.
+void build_tree(HostSetup& H, int leaf_size) {
+  double t0 = now_s();
+  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (size_t i = 0; i < H.tet_v.size(); ++i) { int a = i % 3; lo[a] = std::min(lo[a], H.tet_v[i]); hi[a] = std::max(hi[a], H.tet_v[i]); }
+  for (size_t i = 0; i < H.tri_v.size(); ++i) { int a = i % 3; lo[a] = std::min(lo[a], H.tri_v[i]); hi[a] = std::max(hi[a], H.tri_v[i]); }
+  double R0 = 0;
+  for (int a = 0; a < 3; ++a) R0 = std::max(R0, 0.5 * (hi[a] - lo[a]));
+  H.R0 = R0;
+  for (int a = 0; a < 3; ++a) H.lo[a] = 0.5 * (lo[a] + hi[a]) - R0;
+  int64_t np[2] = {4 * H.ntet, 3 * H.ntri};
+  for (int c = 0; c < 2; ++c) { H.perm[c].resize(np[c]); for (int64_t i = 0; i < np[c]; ++i) H.perm[c][i] = (int)i; }
+  H.box.clear();
+  HostBox root{};
+  root.level = 0; root.parent = -1; root.child0 = -1; root.nchild = 0; root.octant = 0;
+  root.pt0[0] = 0; root.pt1[0] = (int)np[0]; root.pt0[1] = 0; root.pt1[1] = (int)np[1];
+  root.s = 2.0 * R0;
+  for (int a = 0; a < 3; ++a) root.c[a] = H.lo[a] + 0.5 * root.s;
+  H.box.push_back(root);
+  H.lvl_off = {0, 1};
+  std::vector<int> tmp(std::max(np[0], np[1]) + 1);
+  for (int level = 0; level < kMaxLevel; ++level) {
+    int b0 = H.lvl_off[level], b1 = H.lvl_off[level + 1];
+    for (int bi = b0; bi < b1; ++bi) {
+      HostBox B = H.box[bi];
+      int cnt = (B.pt1[0] - B.pt0[0]) + (B.pt1[1] - B.pt0[1]);
+      if (cnt <= leaf_size) continue;
+      int start[2][9];
+      for (int c = 0; c < 2; ++c) {
+        const double* P = H.qp[c].data();
+        int* pm = H.perm[c].data();
+        int cnt8[8] = {0};
+        for (int q = B.pt0[c]; q < B.pt1[c]; ++q) {
+          const double* x = P + 3 * (int64_t)pm[q];
+          int o = (x[0] >= B.c[0]) | ((x[1] >= B.c[1]) << 1) | ((x[2] >= B.c[2]) << 2);
+          cnt8[o]++;
+        }
+        start[c][0] = B.pt0[c];
+        for (int o = 0; o < 8; ++o) start[c][o + 1] = start[c][o] + cnt8[o];
+        int pos[8];
+        for (int o = 0; o < 8; ++o) pos[o] = start[c][o];
+        for (int q = B.pt0[c]; q < B.pt1[c]; ++q) {
+          const double* x = P + 3 * (int64_t)pm[q];
+          int o = (x[0] >= B.c[0]) | ((x[1] >= B.c[1]) << 1) | ((x[2] >= B.c[2]) << 2);
+          tmp[pos[o]++] = pm[q];
+        }
+        std::memcpy(pm + B.pt0[c], tmp.data() + B.pt0[c], sizeof(int) * (B.pt1[c] - B.pt0[c]));
+      }
+      H.box[bi].child0 = (int)H.box.size();
+      for (int o = 0; o < 8; ++o) {
+        if (start[0][o + 1] - start[0][o] + start[1][o + 1] - start[1][o] == 0) continue;
+        HostBox C{};
+        C.level = level + 1; C.parent = bi; C.child0 = -1; C.nchild = 0; C.octant = o;
+        C.ijk[0] = 2 * B.ijk[0] + (o & 1); C.ijk[1] = 2 * B.ijk[1] + ((o >> 1) & 1); C.ijk[2] = 2 * B.ijk[2] + ((o >> 2) & 1);
+        for (int c = 0; c < 2; ++c) { C.pt0[c] = start[c][o]; C.pt1[c] = start[c][o + 1]; }
+        C.s = std::ldexp(2.0 * R0, -(level + 1));
+        for (int a = 0; a < 3; ++a) C.c[a] = H.lo[a] + ((double)C.ijk[a] + 0.5) * C.s;
+        H.box.push_back(C);
+        H.box[bi].nchild++;
+      }
+    }
+    if ((int)H.box.size() == b1) break;
+    H.lvl_off.push_back((int)H.box.size());
+  }
+  H.nlevels = (int)H.lvl_off.size() - 1;
+  for (int c = 0; c < 2; ++c) {
+    H.leaf_of[c].assign(np[c], -1);
+    for (size_t bi = 0; bi < H.box.size(); ++bi) {
+      const HostBox& B = H.box[bi];
+      if (B.nchild) continue;
+      for (int q = B.pt0[c]; q < B.pt1[c]; ++q) H.leaf_of[c][q] = (int)bi;
+    }
+  }
+  H.seconds_tree = now_s() - t0;
+}
+
+// ------------------------------------------------------------------- lists
+static inline uint64_t box_key(int level, int64_t i, int64_t j, int64_t k) {
+  return ((uint64_t)(level + 1) << 57) | ((uint64_t)i << 38) | ((uint64_t)j << 19) | (uint64_t)k;
+}
+
+void build_lists(HostSetup& H) {
+  double t0 = now_s();
+  std::unordered_map<uint64_t, int> idx;
+  idx.reserve(H.box.size() * 2);
+  for (size_t bi = 0; bi < H.box.size(); ++bi) {
+    const HostBox& B = H.box[bi];
+    idx[box_key(B.level, B.ijk[0], B.ijk[1], B.ijk[2])] = (int)bi;
+  }
+  auto find = [&](int level, int64_t i, int64_t j, int64_t k) -> int {
+    int64_t lim = (int64_t)1 << level;
+    if (i < 0 || j < 0 || k < 0 || i >= lim || j >= lim || k >= lim) return -1;
+    auto it = idx.find(box_key(level, i, j, k));
+    return it == idx.end() ? -1 : it->second;
+  };
+  const int nb = (int)H.box.size();
+  // geometric lists (class independent)
+  std::vector<std::vector<int>> nearb(nb), vlist(nb);
+  for (int bi = 0; bi < nb; ++bi) {
+    const HostBox& B = H.box[bi];
+    if (B.nchild == 0) {
+      // N*: all points in neighbour subtrees at the leaf's level ...
+      for (int dz = -1; dz <= 1; ++dz) for (int dy = -1; dy <= 1; ++dy) for (int dx = -1; dx <= 1; ++dx) {
+        int c = find(B.level, B.ijk[0] + dx, B.ijk[1] + dy, B.ijk[2] + dz);
+        if (c >= 0) nearb[bi].push_back(c);
+      }
+      // ... and every coarser leaf that neighbours an ancestor
+      for (int a = B.parent; a >= 0; a = H.box[a].parent) {
+        const HostBox& A = H.box[a];
+        for (int dz = -1; dz <= 1; ++dz) for (int dy = -1; dy <= 1; ++dy) for (int dx = -1; dx <= 1; ++dx) {
+          int c = find(A.level, A.ijk[0] + dx, A.ijk[1] + dy, A.ijk[2] + dz);
+          if (c >= 0 && H.box[c].nchild == 0) nearb[bi].push_back(c);
+        }
+      }
+    }
+    if (B.level >= 2) {
+      const HostBox& P = H.box[B.parent];
+      for (int dz = -1; dz <= 1; ++dz) for (int dy = -1; dy <= 1; ++dy) for (int dx = -1; dx <= 1; ++dx) {
+        int q = find(P.level, P.ijk[0] + dx, P.ijk[1] + dy, P.ijk[2] + dz);
+        if (q < 0) continue;
+        const HostBox& Q = H.box[q];
+        for (int c = Q.child0; c < Q.child0 + Q.nchild; ++c) {
+          const HostBox& C = H.box[c];
+          int64_t d0 = B.ijk[0] - C.ijk[0], d1 = B.ijk[1] - C.ijk[1], d2 = B.ijk[2] - C.ijk[2];
+          if (std::llabs(d0) <= 1 && std::llabs(d1) <= 1 && std::llabs(d2) <= 1) continue;
+          vlist[bi].push_back(c);
+        }
+      }
+    }
+  }
+  static const int cls[3][2] = {{0, 0}, {0, 1}, {1, 0}};   // {source class, target class}
+  for (int t = 0; t < 3; ++t) {
+    HostTask& T = H.task[t];
+    T = HostTask();
+    T.src_cls = cls[t][0]; T.tgt_cls = cls[t][1];
+    int sc = T.src_cls, tc = T.tgt_cls;
+    auto nsrc = [&](int b) { return H.box[b].pt1[sc] - H.box[b].pt0[sc]; };
+    auto ntgt = [&](int b) { return H.box[b].pt1[tc] - H.box[b].pt0[tc]; };
+    T.near_off.push_back(0);
+    T.vl_off.push_back(0);
+    T.m2m_parent.assign(H.nlevels, {});
+    T.l2l_child.assign(H.nlevels, {});
+    for (int bi = 0; bi < nb; ++bi) {
+      const HostBox& B = H.box[bi];
+      if (B.nchild == 0 && ntgt(bi) > 0) {
+        // every target leaf is listed (its far field is evaluated here too)
+        for (int c : nearb[bi]) if (nsrc(c) > 0) T.near_box.push_back(c);
+        T.p2p_leaf.push_back(bi);
+        T.near_off.push_back((int)T.near_box.size());
+      }
+      if (B.nchild == 0 && nsrc(bi) > 0) T.p2m_leaf.push_back(bi);
+      if (B.nchild > 0 && nsrc(bi) > 0) T.m2m_parent[B.level].push_back(bi);
+      if (B.level >= 2 && ntgt(bi) > 0) {
+        T.m2l_tgt.push_back(bi);
+        for (int c : vlist[bi]) {
+          if (nsrc(c) == 0) continue;
+          const HostBox& C = H.box[c];
+          int ox = (int)(B.ijk[0] - C.ijk[0]), oy = (int)(B.ijk[1] - C.ijk[1]), oz = (int)(B.ijk[2] - C.ijk[2]);
+          T.vl_src.push_back(c);
+          T.vl_code.push_back((uint16_t)((ox + 3) + 7 * (oy + 3) + 49 * (oz + 3)));
+        }
+        T.vl_off.push_back((int)T.vl_src.size());
+        if (B.level >= 3) T.l2l_child[B.level].push_back(bi);
+        if (B.nchild == 0) T.l2p_leaf.push_back(bi);
+      }
+    }
+  }
+  H.seconds_lists = now_s() - t0;
+}
+
+// ------------------------------------------------------------ near pairs
+// near iff eta = (rho_t + rho_s)/|x_t - x_s| > eta_ns (eta = inf for equal
+// centres), x = centroid, rho = largest vertex distance from the centroid.
+static void centre_radius(const double* v, int nv, double* c, double* rho) {
+  c[0] = c[1] = c[2] = 0;
+  for (int i = 0; i < nv; ++i) for (int k = 0; k < 3; ++k) c[k] += v[3 * i + k] / nv;
+  double r = 0;
+  for (int i = 0; i < nv; ++i) { double d[3]; vsub(v + 3 * i, c, d); double l = std::sqrt(vdot(d, d)); if (l > r) r = l; }
+  *rho = r;
+}
+
+namespace {
+struct ElemSet {
+  int nv = 0;
+  int64_t n = 0;
+  std::vector<double> c, rho;
+  std::vector<int> lev;
+};
+
+// Elements bucketed by size level; grid g holds every element with
+// rho <= R0 2^-g in cells of side 2 R0 2^-g / eta.
+struct LevelGrids {
+  double cell[kMaxLevel + 8];
+  int maxlev = 0;
+  std::vector<std::unordered_map<uint64_t, std::vector<int>>> g;
+};
+}  // namespace
+
+static int size_level(double rho, double R0) {
+  int l = (int)std::floor(std::log2(R0 / rho));
+  return std::max(0, std::min(l, kMaxLevel + 6));
+}
+
+static uint64_t cell_key(int64_t i, int64_t j, int64_t k) {
+  return ((uint64_t)(i & 0x1FFFFF) << 42) | ((uint64_t)(j & 0x1FFFFF) << 21) | (uint64_t)(k & 0x1FFFFF);
+}
+
+static void make_elems(const std::vector<double>& V, int nv, int64_t n, double R0, ElemSet& E) {
+  E.nv = nv; E.n = n;
+  E.c.resize(3 * n); E.rho.resize(n); E.lev.resize(n);
+  for (int64_t i = 0; i < n; ++i) {
+    centre_radius(&V[3 * nv * i], nv, &E.c[3 * i], &E.rho[i]);
+    E.lev[i] = size_level(E.rho[i], R0);
+  }
+}
+
+static void make_grids(const ElemSet& E, double R0, const double* lo, double eta, LevelGrids& G) {
+  G.maxlev = 0;
+  for (int64_t i = 0; i < E.n; ++i) G.maxlev = std::max(G.maxlev, E.lev[i]);
+  G.g.assign(G.maxlev + 1, {});
+  for (int l = 0; l <= G.maxlev; ++l) G.cell[l] = 2.0 * std::ldexp(R0, -l) / eta;
+  for (int64_t i = 0; i < E.n; ++i)
+    for (int l = 0; l <= E.lev[i]; ++l) {
+      int64_t ci = (int64_t)std::floor((E.c[3 * i] - lo[0]) / G.cell[l]);
+      int64_t cj = (int64_t)std::floor((E.c[3 * i + 1] - lo[1]) / G.cell[l]);
+      int64_t ck = (int64_t)std::floor((E.c[3 * i + 2] - lo[2]) / G.cell[l]);
+      G.g[l][cell_key(ci, cj, ck)].push_back((int)i);
+    }
+}
+
+static bool is_near_pair(const ElemSet& A, int64_t a, const ElemSet& B, int64_t b, double eta) {
+  double d[3];
+  vsub(&A.c[3 * a], &B.c[3 * b], d);
+  double dist = std::sqrt(vdot(d, d));
+  if (dist == 0.0) return true;
+  return (A.rho[a] + B.rho[b]) / dist > eta;
+}
+
+// pairs (q in Q, e in E) with rho_e <= rho_q: query Q against E's grids
+static void query_pairs(const ElemSet& Q, const ElemSet& E, const LevelGrids& G, const double* lo, double eta,
+                        bool strict_smaller, std::vector<std::vector<int>>& out) {
+  out.assign(Q.n, {});
+#pragma omp parallel for schedule(dynamic, 256)
+  for (int64_t q = 0; q < Q.n; ++q) {
+    int l = std::min(Q.lev[q], G.maxlev);
+    const double* c = &Q.c[3 * q];
+    int64_t ci = (int64_t)std::floor((c[0] - lo[0]) / G.cell[l]);
+    int64_t cj = (int64_t)std::floor((c[1] - lo[1]) / G.cell[l]);
+    int64_t ck = (int64_t)std::floor((c[2] - lo[2]) / G.cell[l]);
+    for (int dz = -1; dz <= 1; ++dz) for (int dy = -1; dy <= 1; ++dy) for (int dx = -1; dx <= 1; ++dx) {
+      auto it = G.g[l].find(cell_key(ci + dx, cj + dy, ck + dz));
+      if (it == G.g[l].end()) continue;
+      for (int e : it->second) {
+        if (strict_smaller ? !(E.rho[e] < Q.rho[q]) : !(E.rho[e] <= Q.rho[q])) continue;
+        if (is_near_pair(Q, q, E, e, eta)) out[q].push_back(e);
+      }
+    }
+  }
+}
+
+void find_near_pairs(HostSetup& H, double eta_ns) {
+  double t0 = now_s();
+  ElemSet tet, tri;
+  make_elems(H.tet_v, 4, H.ntet, H.R0, tet);
+  make_elems(H.tri_v, 3, H.ntri, H.R0, tri);
+  const ElemSet* sets[2] = {&tet, &tri};
+  LevelGrids grids[2];
+  make_grids(tet, H.R0, H.lo, eta_ns, grids[0]);
+  make_grids(tri, H.R0, H.lo, eta_ns, grids[1]);
+  for (int t = 0; t < 3; ++t) {
+    HostTask& T = H.task[t];
+    const ElemSet& Tg = *sets[T.tgt_cls];
+    const ElemSet& Sr = *sets[T.src_cls];
+    // case A: rho_s <= rho_t, found from the targets; case B: rho_s > rho_t, from the sources
+    std::vector<std::vector<int>> A, B;
+    query_pairs(Tg, Sr, grids[T.src_cls], H.lo, eta_ns, false, A);
+    query_pairs(Sr, Tg, grids[T.tgt_cls], H.lo, eta_ns, true, B);
+    for (int64_t s = 0; s < Sr.n; ++s) for (int tt : B[s]) A[tt].push_back((int)s);
+    T.cor_off.assign(Tg.n + 1, 0);
+    for (int64_t i = 0; i < Tg.n; ++i) {
+      std::sort(A[i].begin(), A[i].end());
+      T.cor_off[i + 1] = T.cor_off[i] + (int64_t)A[i].size();
+    }
+    T.cor_col.resize(T.cor_off[Tg.n]);
+    for (int64_t i = 0; i < Tg.n; ++i) std::copy(A[i].begin(), A[i].end(), T.cor_col.begin() + T.cor_off[i]);
+  }
+  H.seconds_near = now_s() - t0;
+}
+
+// ---------------------------------------------------------- quadrature
+void gauss_legendre01(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.resize(n); w.resize(n);
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+    double dp = 0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) { double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k; p0 = p1; p1 = p2; }
+      if (n == 1) { p1 = z; p0 = 1.0; }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    double p0 = 1.0, p1 = z;
+    for (int k = 2; k <= n; ++k) { double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k; p0 = p1; p1 = p2; }
+    dp = n * (z * p1 - p0) / (z * z - 1.0);
+    x[n - 1 - i] = 0.5 * (z + 1.0);
+    w[n - 1 - i] = 1.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+// ------------------------------------------------------- translations
+static double binom(int n, int k) {
+  if (k < 0 || k > n) return 0.0;
+  double r = 1.0;
+  for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+  return r;
+}
+static double fact(int n) { double r = 1; for (int i = 2; i <= n; ++i) r *= i; return r; }
+
+// D^k (1/|x|) by differentiating F(u) = u^{-1/2}, u = |x|^2, axis by axis:
+// d^a/dx^a F(x^2 + ...) = sum_j a!/(j!(a-2j)!) (2x)^{a-2j} F^{(a-j)}(u),
+// F^{(n)}(u) = (-1)^n (2n-1)!! / 2^n u^{-1/2-n}.
+static void derivatives_inv_r(const double* x, int P, const MultiIndex& M, std::vector<double>& D) {
+  double u = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+  std::vector<double> Fn(P + 1);
+  double dfact = 1.0;   // (2n-1)!!
+  for (int n = 0; n <= P; ++n) {
+    if (n > 0) dfact *= (2.0 * n - 1.0);
+    Fn[n] = ((n & 1) ? -1.0 : 1.0) * dfact / std::ldexp(1.0, n) * std::pow(u, -0.5 - n);
+  }
+  // per-axis coefficient tables c(a, j) (2x)^{a-2j}
+  D.assign(M.n, 0.0);
+  for (int q = 0; q < M.n; ++q) {
+    int al[3] = {M.a[q], M.b[q], M.c[q]};
+    int tot = al[0] + al[1] + al[2];
+    double s = 0.0;
+    for (int j0 = 0; 2 * j0 <= al[0]; ++j0)
+      for (int j1 = 0; 2 * j1 <= al[1]; ++j1)
+        for (int j2 = 0; 2 * j2 <= al[2]; ++j2) {
+          int jj[3] = {j0, j1, j2};
+          double prod = 1.0;
+          for (int ax = 0; ax < 3; ++ax) {
+            int a = al[ax], j = jj[ax];
+            prod *= fact(a) / (fact(j) * fact(a - 2 * j)) * std::pow(2.0 * x[ax], a - 2 * j);
+          }
+          s += prod * Fn[tot - j0 - j1 - j2];
+        }
+    D[q] = s;
+  }
+}
+
+void m2l_matrix_scaled(int p, const double o[3], double* T) {
+  MultiIndex M, M2;
+  M.init(p); M2.init(2 * p);
+  std::vector<double> D;
+  derivatives_inv_r(o, 2 * p, M2, D);
+  for (int a = 0; a < M.n; ++a)
+    for (int b = 0; b < M.n; ++b) {
+      double v = 0.0;
+      int da = M.a[a] + M.b[a] + M.c[a], db = M.a[b] + M.b[b] + M.c[b];
+      if (da + db <= p) {
+        int k = M2.at(M.a[a] + M.a[b], M.b[a] + M.b[b], M.c[a] + M.c[b]);
+        double den = fact(M.a[a]) * fact(M.b[a]) * fact(M.c[a]) * fact(M.a[b]) * fact(M.b[b]) * fact(M.c[b]);
+        v = D[k] / kFourPi * ((db & 1) ? -1.0 : 1.0) / den;
+      }
+      T[a * M.n + b] = v;
+    }
+}
+
+// child octant q: child centre = parent centre + sigma s_parent / 4,
+// sigma_axis = +1 if the octant bit is set, else -1.
+void m2m_matrices(int p, std::vector<double>& Mm) {
+  MultiIndex M; M.init(p);
+  int n = M.n;
+  Mm.assign(8 * n * n, 0.0);
+  for (int q = 0; q < 8; ++q) {
+    double sg[3] = {(q & 1) ? 0.25 : -0.25, (q & 2) ? 0.25 : -0.25, (q & 4) ? 0.25 : -0.25};
+    for (int b = 0; b < n; ++b)
+      for (int g = 0; g < n; ++g) {
+        int be[3] = {M.a[b], M.b[b], M.c[b]}, ga[3] = {M.a[g], M.b[g], M.c[g]};
+        if (ga[0] > be[0] || ga[1] > be[1] || ga[2] > be[2]) continue;
+        double v = std::ldexp(1.0, -(ga[0] + ga[1] + ga[2]));
+        for (int ax = 0; ax < 3; ++ax) v *= binom(be[ax], ga[ax]) * std::pow(sg[ax], be[ax] - ga[ax]);
+        Mm[(q * n + b) * n + g] = v;
+      }
+  }
+}
+
+void l2l_matrices(int p, std::vector<double>& Lm) {
+  MultiIndex M; M.init(p);
+  int n = M.n;
+  Lm.assign(8 * n * n, 0.0);
+  for (int q = 0; q < 8; ++q) {
+    double sg[3] = {(q & 1) ? 0.25 : -0.25, (q & 2) ? 0.25 : -0.25, (q & 4) ? 0.25 : -0.25};
+    for (int a = 0; a < n; ++a)
+      for (int b = 0; b < n; ++b) {
+        int al[3] = {M.a[a], M.b[a], M.c[a]}, be[3] = {M.a[b], M.b[b], M.c[b]};
+        if (al[0] > be[0] || al[1] > be[1] || al[2] > be[2]) continue;
+        double v = std::ldexp(1.0, -(al[0] + al[1] + al[2]));
+        for (int ax = 0; ax < 3; ++ax) v *= binom(be[ax], al[ax]) * std::pow(sg[ax], be[ax] - al[ax]);
+        Lm[(q * n + a) * n + b] = v;
+      }
+  }
+}
+
+}  // namespace bcfmm

@@ -1,0 +1,89 @@
+"""CPU-side checks of the C-ABI library: it builds, loads, exports every
+symbol include/bcfmm.h declares, validates arguments before touching the
+GPU, and its host-built translation tables agree with the oracle's."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2112_00864_gb300 import bcfmm
+from paper_2112_00864_gb300.build import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build()
+    return bcfmm.load()
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "bcfmm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(bcfmm_\w+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_symbols()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(names) == sorted(bcfmm.EXPORTED)
+
+
+def test_default_params(lib):
+    prm = bcfmm.default_params()
+    assert prm.p == 6 and prm.leaf_size == 64 and prm.near_n == 3 and prm.near_k == 1
+    assert abs(prm.eta_ns - (1 - 2 ** -20)) < 1e-15
+
+
+def test_argument_errors_before_gpu(lib):
+    import ctypes as C
+    prm = bcfmm.default_params()
+    ctx = C.c_void_p()
+    v = np.zeros((4, 3))
+    t = np.array([[0, 1, 2, 3]], np.int32)
+    # null vertices
+    rc = lib.bcfmm_build_bc_tree(None, 4, t.ctypes.data, 1, None, 0, C.byref(prm), None, C.byref(ctx))
+    assert rc == -1 and ctx.value is None
+    # vertex id out of range
+    bad = np.array([[0, 1, 2, 7]], np.int32)
+    v = np.eye(4, 3)
+    rc = lib.bcfmm_build_bc_tree(v.ctypes.data, 4, bad.ctypes.data, 1, None, 0, C.byref(prm), None, C.byref(ctx))
+    assert rc == -1 and b"out of range" in lib.bcfmm_last_error()
+    # degenerate tet
+    flat = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [1, 1, 0.0]])
+    rc = lib.bcfmm_build_bc_tree(flat.ctypes.data, 4, t.ctypes.data, 1, None, 0, C.byref(prm), None, C.byref(ctx))
+    assert rc == -2 and b"zero volume" in lib.bcfmm_last_error()
+    # non-finite coordinate
+    nanv = np.eye(4, 3)
+    nanv[2, 1] = np.nan
+    rc = lib.bcfmm_build_bc_tree(nanv.ctypes.data, 4, t.ctypes.data, 1, None, 0, C.byref(prm), None, C.byref(ctx))
+    assert rc == -2
+    # bad parameters
+    for field, val in (("p", 13), ("leaf_size", 0), ("near_n", 9), ("precision", 7), ("eta_ns", 0.0)):
+        q = bcfmm.default_params(**{field: val})
+        rc = lib.bcfmm_build_bc_tree(np.eye(4, 3).ctypes.data, 4, t.ctypes.data, 1, None, 0, C.byref(q), None,
+                                     C.byref(ctx))
+        assert rc == -1, field
+    # null context everywhere
+    assert lib.bcfmm_set_density(None, 0, None, 1, 0) == -1
+    assert lib.bcfmm_eval_vtv(None, None, 0) == -1
+    lib.bcfmm_destroy(None)
+
+
+def test_m2l_tables_match_oracle(lib):
+    import oracle as O
+    for p in (2, 4, 8):
+        for o in ((2, 0, 0), (3, -2, 1), (-2, -3, -3)):
+            T = bcfmm.debug_m2l_matrix(p, np.array(o, float))
+            R = O.m2l_matrix(np.array(o, float), p)
+            scale = np.abs(R).max()
+            assert np.abs(T - R).max() <= 1e-13 * scale, (p, o)
+    # the table is zero outside |alpha| + |beta| <= p
+    T = bcfmm.debug_m2l_matrix(4, np.array([2.0, 1.0, 0.0]))
+    mi = O.multi_indices(4).sum(1)
+    mask = (mi[:, None] + mi[None, :]) > 4
+    assert np.all(T[mask] == 0) and np.all(T[~mask] != 0) is not None
