@@ -1,0 +1,359 @@
+"""Benchmark: VtV + VtB target points per second on the unit-ball BC mesh.
+
+Workload (the paper's volume-potential tasks, Sec. 5 / Algorithms 1-2):
+unit ball bounded by the level-4 icosphere (5120 triangles), radially graded
+BC tet mesh (~1.9e5 tets, ~7.7e5 tet quadrature points), density f = 1.
+One step = set_density + eval_vtv + eval_vtb (one pass of the whole hot
+path).  value = (4 ntet + 3 ntri) * ndens / step time, summed over ranks.
+
+Accuracy gate: the chosen form is compared with the FP64 CPU oracle (direct
+definition, O1) on sampled target elements; rel L2 error must be <= 1e-6.
+Also reported: the plain FP64 GPU path on the same workload, the roofline of
+the dominant kernel (live CUDA events on the library's stream) and the CPU
+oracle's throughput on a bounded sample (cpu_baseline).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "VtV+VtB target pts/s at rel err ≤1e-6: chosen form vs plain FP64, 1 GB300"
+WORKLOAD = {"workload": "unit ball BC mesh: icosphere level 4 (5120 triangles), radially graded tets, f=1",
+            "mesh": "ball_bc_mesh(level=4, radial=0.35)"}
+CHOSEN = dict(p=6, eta0=0.5, leaf_size=64, precision="fp32")
+PLAIN = dict(p=6, eta0=0.5, leaf_size=64, precision="fp64")
+SAMPLE_TARGETS = 64        # per task, for the accuracy gate and the CPU baseline
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_inputs():
+    from paper_2112_00864_gb300.inputs import ball_bc_mesh
+    m = ball_bc_mesh(4, radial=0.35)
+    f = np.ones((1, m.ntet))
+    return m, f
+
+
+def sample_targets(m, seed=11):
+    rng = np.random.default_rng(seed)
+    return (np.sort(rng.choice(m.ntet, SAMPLE_TARGETS, replace=False)),
+            np.sort(rng.choice(m.ntri, SAMPLE_TARGETS, replace=False)))
+
+
+def oracle_sample(m, f, tv, tb):
+    """O1 on the sampled targets; returns (u_vtv, u_vtb, seconds, cores)."""
+    import oracle as O
+    cores = len(os.sched_getaffinity(0))
+    t0 = time.perf_counter()
+    uv = O.direct("vtv", m, f, targets=tv, nthreads=cores)[0]
+    ub = O.direct("vtb", m, f, targets=tb, nthreads=cores)[0]
+    return uv, ub, time.perf_counter() - t0, cores
+
+
+def rel_err(u, ref, size):
+    a, b = u / size, ref / size
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b)), float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def launches_per_step(stats):
+    """Kernels of this library launched by one set_density + eval_vtv + eval_vtb."""
+    L = stats["nlevels"]
+    per_eval = 1 + 1 + L + 1 + max(0, L - 3) + 1 + 1      # weights, P2M, M2M per level, M2L, L2L, P2P+L2P, sums
+    return 2 * per_eval
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2112_00864_gb300 import bcfmm
+    from paper_2112_00864_gb300.build import build
+    build()
+    m, f = make_inputs()
+    npts = (4 * m.ntet + 3 * m.ntri) * f.shape[0]
+    vol = np.abs(np.einsum("ij,ij->i", np.cross(m.verts[m.tets[:, 1]] - m.verts[m.tets[:, 0]],
+                                                 m.verts[m.tets[:, 2]] - m.verts[m.tets[:, 0]]),
+                           m.verts[m.tets[:, 3]] - m.verts[m.tets[:, 0]])) / 6
+    area = 0.5 * np.linalg.norm(np.cross(m.verts[m.tris[:, 1]] - m.verts[m.tris[:, 0]],
+                                         m.verts[m.tris[:, 2]] - m.verts[m.tris[:, 0]]), axis=1)
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    ctx = bcfmm.Context.from_mesh(m, stream=stream, timing=1, **CHOSEN)
+    setup_s = time.perf_counter() - t0
+    f_dev = torch.tensor(f, device="cuda")
+    out_v = torch.empty((1, m.ntet), dtype=torch.float64, device="cuda")
+    out_b = torch.empty((1, m.ntri), dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        ctx.set_density(bcfmm.VOLUME, f_dev)
+        ctx.eval_vtv(out_v)
+        ctx.eval_vtb(out_b)
+
+    def timed(fn, K):
+        times, stages = [], []
+        for _ in range(K):
+            flush.fill_(1.0)                       # L2 flush between timed steps
+            torch.cuda.synchronize()
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record(stream)
+            fn()
+            e.record(stream)
+            torch.cuda.synchronize()
+            times.append(s.elapsed_time(e))
+            st = ctx.stats()["stage_ms"]
+            stages.append((st["vtv"], st["vtb"]))
+        return times, stages
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    times, stages = timed(step, args.steps)
+    clk = clocks.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    ms = float(np.mean(times))
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = npts * world / (ms * 1e-3)
+
+    # end to end through the C ABI with host buffers (pinned), copies inside
+    f_host = torch.tensor(f).pin_memory()
+    hv = torch.empty((1, m.ntet), dtype=torch.float64).pin_memory()
+    hb = torch.empty((1, m.ntri), dtype=torch.float64).pin_memory()
+    hv_np, hb_np, fh_np = hv.numpy(), hb.numpy(), f_host.numpy()
+
+    def step_e2e():
+        ctx.set_density(bcfmm.VOLUME, fh_np)
+        ctx.eval_vtv(hv_np)
+        ctx.eval_vtb(hb_np)
+
+    for _ in range(2):
+        step_e2e()
+    e2e_times, _ = timed(step_e2e, max(3, args.steps // 2))
+    e2e_ms = float(np.mean(e2e_times))
+    st = ctx.stats()
+    u_v, u_b = out_v.cpu().numpy()[0], out_b.cpu().numpy()[0]
+
+    # plain FP64 GPU path, same workload and tree parameters
+    plain = bcfmm.Context.from_mesh(m, stream=stream, **PLAIN)
+    pv = torch.empty_like(out_v)
+    pb = torch.empty_like(out_b)
+    plain.set_density(bcfmm.VOLUME, f_dev)
+    plain.eval_vtv(pv); plain.eval_vtb(pb)
+    torch.cuda.synchronize()
+    pt = []
+    for _ in range(3):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        plain.set_density(bcfmm.VOLUME, f_dev)
+        plain.eval_vtv(pv); plain.eval_vtb(pb)
+        e.record(stream)
+        torch.cuda.synchronize()
+        pt.append(s.elapsed_time(e))
+    plain_ms = float(np.mean(pt))
+    plain_v, plain_b = pv.cpu().numpy()[0], pb.cpu().numpy()[0]
+    plain.close()
+
+    result = None
+    if rank == 0:
+        tv, tb = sample_targets(m)
+        ov, ob, osec, cores = oracle_sample(m, f, tv, tb)
+        err = {"vtv": rel_err(u_v[tv], ov, vol[tv]), "vtb": rel_err(u_b[tb], ob, area[tb])}
+        err_plain = {"vtv": rel_err(plain_v[tv], ov, vol[tv]), "vtb": rel_err(plain_b[tb], ob, area[tb])}
+        pk, src = peaks()
+        # per-stage device times (mean over the timed steps): [clear, P2M+M2M, M2L, L2L, L2P+P2P, sums]
+        sv = np.mean([s[0] for s in stages], axis=0)
+        sb = np.mean([s[1] for s in stages], axis=0)
+        p2p_ms = sv[4] + sb[4]
+        m2l_ms = sv[2] + sb[2]
+        sm_clk = clk.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
+        pairs = st["vtv"]["p2p_pairs"] + st["vtb"]["p2p_pairs"]
+        ops_p2p = 7.0 * pairs                                        # FP32-pipe ops per pair
+        fp32_peak = 152 * 128 * pk.get("sm_max_mhz", 2070.0) * 1e6  # FP32-pipe ops/s at max clock
+        m2l_pairs = st["vtv"]["m2l_pairs"] + st["vtb"]["m2l_pairs"]
+        p = st["p"]
+        m2l_flop = 2.0 * math.comb(p + 6, 6) * m2l_pairs
+        roof_p2p = {"kernel": "k_p2p_l2p_f32", "bound": "alu", "achieved": ops_p2p / (p2p_ms * 1e-3) / 1e12,
+                    "peak": fp32_peak / 1e12, "unit": "TFLOP/s", "traffic": None,
+                    "note": "FP32-pipe ops (7 per pair: 3 sub, 1 mul, 2 fma, 1 fma) per s vs 152 SMs x 128 lanes "
+                            "x max SM clock; the rsqrt on MUFU caps it at 7/8 of this peak",
+                    "ms_per_step": float(p2p_ms), "pairs": int(pairs)}
+        roof_p2p["frac"] = roof_p2p["achieved"] / roof_p2p["peak"]
+        roof_m2l = {"kernel": "k_m2l_simt", "bound": "alu", "achieved": m2l_flop / (m2l_ms * 1e-3) / 1e12,
+                    "peak": 2 * fp32_peak / 1e12, "unit": "TFLOP/s", "traffic": None,
+                    "note": "algorithmic FMA flops 2*C(p+6,6) per box pair vs FP32 FMA peak",
+                    "ms_per_step": float(m2l_ms), "pairs": int(m2l_pairs)}
+        roof_m2l["frac"] = roof_m2l["achieved"] / roof_m2l["peak"]
+        dominant = roof_p2p if p2p_ms >= m2l_ms else roof_m2l
+        roofline = dict(dominant)
+        roofline["peak_source"] = src + " (derived: unit counts x max SM clock)"
+        osamp_pts = 4 * len(tv) + 3 * len(tb)
+        result = {
+            "metric": METRIC, "value": value, "unit": "target pts/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 (P2P, expansions, M2L); f64 setup, near corrections, sums",
+            "data": "synthetic: analytic BC mesh and density (no dataset)",
+            "config": dict(WORKLOAD, ntet=m.ntet, ntri=m.ntri, ndens=int(f.shape[0]), l2="flushed between steps",
+                           **{k: v for k, v in CHOSEN.items()}),
+            "accuracy": {"rel_l2_vs_oracle": {k: v[0] for k, v in err.items()},
+                         "rel_max_vs_oracle": {k: v[1] for k, v in err.items()},
+                         "sample_targets_per_task": SAMPLE_TARGETS,
+                         "ok": bool(max(v[0] for v in err.values()) <= 1e-6)},
+            "plain_fp64": {"value": npts / (plain_ms * 1e-3), "ms_per_step": plain_ms,
+                           "rel_l2_vs_oracle": {k: v[0] for k, v in err_plain.items()},
+                           "chosen_over_plain": plain_ms / ms},
+            "roofline": roofline,
+            "stages_ms": {"vtv": [float(x) for x in sv], "vtb": [float(x) for x in sb],
+                          "names": ["weights+clear", "P2M+M2M", "M2L", "L2L", "L2P+P2P", "sums+corrections"]},
+            "roofline_other": roof_m2l if dominant is roof_p2p else roof_p2p,
+            "cpu_baseline": {"value": osamp_pts / osec, "unit": "target pts/s", "cores": cores, "kind": "oracle",
+                             "sample": f"O1 direct definition on {len(tv)} VtV + {len(tb)} VtB sampled target "
+                                       f"elements of the same workload ({osec:.1f} s)"},
+            "e2e": {"value": npts / (e2e_ms * 1e-3), "unit": "target pts/s",
+                    "h2d_bytes_per_step": int(f.nbytes), "d2h_bytes_per_step": int(8 * (m.ntet + m.ntri))},
+            "gpu_launches": launches_per_step(st) * args.steps,
+            "clocks": clk,
+            "setup_s": setup_s,
+        }
+    ctx.close()
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return result
+
+
+def run_reference(args):
+    """The oracle arm: O1 (FP64 CPU direct definition) on bounded samples of
+    the same workload, timed per step on the host cores."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return None
+    m, f = make_inputs()
+    import oracle as O
+    O.build_lib()
+    cores = len(os.sched_getaffinity(0))
+    per = 8
+    rng = np.random.default_rng(5)
+    for _ in range(args.warmup):
+        O.direct("vtv", m, f, targets=rng.choice(m.ntet, 2, replace=False), nthreads=cores)
+    times, pts = [], 0
+    for _ in range(args.steps):
+        tv = np.sort(rng.choice(m.ntet, per, replace=False))
+        tb = np.sort(rng.choice(m.ntri, per, replace=False))
+        t0 = time.perf_counter()
+        O.direct("vtv", m, f, targets=tv, nthreads=cores)
+        O.direct("vtb", m, f, targets=tb, nthreads=cores)
+        times.append(time.perf_counter() - t0)
+        pts += 4 * per + 3 * per
+    sec = float(np.sum(times))
+    value = pts / sec
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "target pts/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic: analytic BC mesh and density (no dataset)",
+        "config": dict(WORKLOAD, ntet=m.ntet, ntri=m.ntri, ndens=1, l2="n/a (CPU)"),
+        "cpu_baseline": {"value": value, "unit": "target pts/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{per} VtV + {per} VtB random target elements per step (O1, FP64)"},
+        "e2e": {"value": value, "unit": "target pts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+    res = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if res is not None:
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -22,9 +22,10 @@
  *                       near_k uniform refinements).
  * The far field goes through truncated Cartesian Taylor expansions of order
  * p (Sec. 3.3) on an adaptive octree of quadrature points (<= leaf_size
- * points per leaf); interaction lists are the children of the parent's
- * neighbours that are not neighbours (Sec. 2), and the near field of a leaf
- * is its extended neighbour list N* (Sec. 3, Lemma 3.1).
+ * points per leaf); same-level boxes are neighbours when their separation
+ * ratio exceeds eta0 (Eq. def:neighbors), interaction lists are the children
+ * of the parent's neighbours that are not neighbours (Sec. 2), and the near
+ * field of a leaf is its extended neighbour list N* (Sec. 3, Lemma 3.1).
  *
  * Conventions for every entry point:
  *  - Return value is a bcfmm_status; nothing throws across this boundary.
@@ -79,6 +80,10 @@ typedef struct {
   int32_t near_k;       /* near rule: uniform refinements of the target; default 1      */
   int32_t precision;    /* bcfmm_precision; default BCFMM_FP64                          */
   int32_t timing;       /* nonzero: record per-stage CUDA-event times of each eval      */
+  double eta0;          /* box neighbours: eta = sqrt(3)/|o| > eta0, o the integer offset
+                           of two same-level box centres (Eq. def:neighbors applied to
+                           boxes); default 0.5 as in Sec. 5; values in (0.866, 1] give the
+                           27 boxes whose closures touch; range 0.3..1                  */
 } bcfmm_params;
 
 /* Fills *prm with the defaults above.  Never fails. */
@@ -145,7 +150,8 @@ void bcfmm_destroy(bcfmm_ctx* ctx);
 
 /*
  * Test hook: the box-scaled M2L matrix of Sec. 3.3 that the library uses,
- * for integer offset o = (x_t - x_s)/s between same-level box centres:
+ * for offset o = (x_t - x_s)/s between same-level box centres (o integer in
+ * use; any nonzero o accepted here):
  *   T[a][b] = D^{a+b}G(o) (-1)^{|b|} / (a! b!),   G = 1/(4 pi |.|),
  * for |a| + |b| <= p (zero otherwise), multi-indices ordered by total
  * degree, then lexicographically descending.  T: host [np][np], np =

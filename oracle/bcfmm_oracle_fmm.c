@@ -18,7 +18,11 @@
  *   a box holding more than Ls points (volume + boundary points together)
  *   is split; a point goes to the child on the upper side of every axis
  *   where its coordinate is >= the box centre; empty children are dropped.
- *   neighbours: same-level boxes whose closures touch (|di|,|dj|,|dk| <= 1).
+ *   neighbours: same-level boxes B, C with separation ratio
+ *         eta(B,C) = (rho_B + rho_C)/|x_B - x_C| > eta0 (Eq. def:sepRatio,
+ *         Eq. def:neighbors), rho = sqrt(3)/2 s the box circumradius; with
+ *         o = (x_B - x_C)/s this is |o|^2 eta0^2 < 3.  eta0 in (sqrt3/2, 1]
+ *         gives the 27 boxes whose closures touch.
  *   interaction list I(B): same-level boxes C, C not a neighbour of B,
  *         parent(C) a neighbour of parent(B).
  *   extended neighbour list N*(b) of a leaf b: all points in the subtrees
@@ -293,9 +297,20 @@ static void build_tree(OTree *T, const double *VP, int64_t nv, const double *BP,
 
 static void free_tree(OTree *T) { free(T->box); free(T->hkey); free(T->hval); free(T->pv); free(T->pb); }
 
-static int adjacent_same_level(const OBox *A, const OBox *B) {
-  for (int a = 0; a < 3; ++a) { int64_t d = A->ijk[a] - B->ijk[a]; if (d < -1 || d > 1) return 0; }
-  return 1;
+static int is_neighbour(const OBox *A, const OBox *B, double eta0) {
+  int64_t o2 = 0;
+  for (int a = 0; a < 3; ++a) { int64_t d = A->ijk[a] - B->ijk[a]; o2 += d * d; }
+  return (double)o2 * eta0 * eta0 < 3.0;
+}
+
+/* all integer offsets o with |o|^2 eta0^2 < 3 */
+static int neighbour_offsets(double eta0, int (*off)[3], int cap) {
+  int R = (int)floor(sqrt(3.0) / eta0) + 1, n = 0;
+  for (int z = -R; z <= R; ++z) for (int y = -R; y <= R; ++y) for (int x = -R; x <= R; ++x) {
+    double o2 = (double)(x*x + y*y + z*z);
+    if (o2 * eta0 * eta0 < 3.0 && n < cap) { off[n][0] = x; off[n][1] = y; off[n][2] = z; ++n; }
+  }
+  return n;
 }
 
 /* ------------------------------------------------------------------ */
@@ -306,7 +321,7 @@ static int adjacent_same_level(const OBox *A, const OBox *B) {
  * targets: requested target elements; out[ndens][ntargets].
  * stats (optional, int64[8]): nbox, nleaf, maxlevel, n_m2l, n_p2p, 0,0,0. */
 int orc_fmm(int task, const double *tets, int64_t ntet, const double *tris, int64_t ntri,
-            const double *dens, int ndens, int p, int Ls, double eta_ns,
+            const double *dens, int ndens, int p, int Ls, double eta0, double eta_ns,
             const double *glx, const double *glw, int n, int k,
             const int64_t *targets, int64_t ntargets, double *out, double *out_fmm_only,
             int nthreads, int64_t *stats) {
@@ -324,6 +339,9 @@ int orc_fmm(int task, const double *tets, int64_t ntet, const double *tris, int6
   for (int64_t i = 0; i < 3*ntri; ++i) for (int a = 0; a < 3; ++a) {
     double x = tris[3*i+a]; if (x < lo[a]) lo[a] = x; if (x > hi[a]) hi[a] = x; }
   OTree T; build_tree(&T, VP, nvp, BP, nbp, lo, hi, Ls);
+  static int noff_cap = 4096;
+  int (*NB)[3] = malloc(sizeof(int[3]) * noff_cap);
+  int nnb = neighbour_offsets(eta0, NB, noff_cap);
 
   int src_is_v = (task != 2), tgt_is_v = (task != 1);
   const double *SP = src_is_v ? VP : BP, *SW = src_is_v ? VW : BW;
@@ -376,13 +394,13 @@ int orc_fmm(int task, const double *tets, int64_t ntet, const double *tris, int6
     if (ta == te) continue;
     OBox *P = &T.box[B->parent];
     double *Tm = malloc(sizeof(double) * np * np);
-    for (int dz = -1; dz <= 1; ++dz) for (int dy = -1; dy <= 1; ++dy) for (int dx = -1; dx <= 1; ++dx) {
-      int qi = hget(&T, P->level, P->ijk[0]+dx, P->ijk[1]+dy, P->ijk[2]+dz);
+    for (int q = 0; q < nnb; ++q) {
+      int qi = hget(&T, P->level, P->ijk[0]+NB[q][0], P->ijk[1]+NB[q][1], P->ijk[2]+NB[q][2]);
       if (qi < 0) continue;
       OBox *Q = &T.box[qi];
       for (int c = 0; c < Q->nkids; ++c) {
         OBox *C = &T.box[Q->kids[c]];
-        if (adjacent_same_level(B, C)) continue;
+        if (is_neighbour(B, C, eta0)) continue;
         int64_t sa, se; SRANGE(C, sa, se);
         if (sa == se) continue;
         double r[3] = { B->c[0]-C->c[0], B->c[1]-C->c[1], B->c[2]-C->c[2] };
@@ -416,9 +434,9 @@ int orc_fmm(int task, const double *tets, int64_t ntet, const double *tris, int6
     int64_t ta, te; TRANGE(B, ta, te);
     if (ta == te) continue;
     /* source ranges of N*(B) */
-    int64_t rng[2 * 27 * 20]; int nr = 0;
-    for (int dz = -1; dz <= 1; ++dz) for (int dy = -1; dy <= 1; ++dy) for (int dx = -1; dx <= 1; ++dx) {
-      int ci = hget(&T, B->level, B->ijk[0]+dx, B->ijk[1]+dy, B->ijk[2]+dz);
+    int64_t *rng = malloc(sizeof(int64_t) * 2 * nnb * 20); int nr = 0;
+    for (int q = 0; q < nnb; ++q) {
+      int ci = hget(&T, B->level, B->ijk[0]+NB[q][0], B->ijk[1]+NB[q][1], B->ijk[2]+NB[q][2]);
       if (ci < 0) continue;
       int64_t sa, se; SRANGE(&T.box[ci], sa, se);
       if (sa < se) { rng[2*nr] = sa; rng[2*nr+1] = se; ++nr; }
@@ -426,8 +444,8 @@ int orc_fmm(int task, const double *tets, int64_t ntet, const double *tris, int6
     int ai = B->parent;
     while (ai >= 0) {
       OBox *A = &T.box[ai];
-      for (int dz = -1; dz <= 1; ++dz) for (int dy = -1; dy <= 1; ++dy) for (int dx = -1; dx <= 1; ++dx) {
-        int ci = hget(&T, A->level, A->ijk[0]+dx, A->ijk[1]+dy, A->ijk[2]+dz);
+      for (int q = 0; q < nnb; ++q) {
+        int ci = hget(&T, A->level, A->ijk[0]+NB[q][0], A->ijk[1]+NB[q][1], A->ijk[2]+NB[q][2]);
         if (ci < 0 || T.box[ci].nkids) continue;
         int64_t sa, se; SRANGE(&T.box[ci], sa, se);
         if (sa < se) { rng[2*nr] = sa; rng[2*nr+1] = se; ++nr; }
@@ -452,6 +470,7 @@ int orc_fmm(int task, const double *tets, int64_t ntet, const double *tris, int6
       }
       for (int r = 0; r < nr; ++r) n_p2p += rng[2*r+1] - rng[2*r];
     }
+    free(rng);
   }
   /* Galerkin test sums and near-rule corrections for the requested targets */
   const double *tel = tgt_is_v ? tets : tris, *sel = src_is_v ? tets : tris;
@@ -489,7 +508,7 @@ int orc_fmm(int task, const double *tets, int64_t ntet, const double *tris, int6
     stats[5] = stats[6] = stats[7] = 0;
   }
   free(VP); free(VW); free(BP); free(BW); free(SWd); free(mom); free(loc); free(phi);
-  midx_free(&M); free_tree(&T);
+  midx_free(&M); free_tree(&T); free(NB);
   return 0;
 }
 

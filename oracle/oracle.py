@@ -25,6 +25,7 @@ TASKS = {"vtv": 0, "vtb": 1, "btv": 2}
 ETA_NS = 1.0 - 2.0 ** -20      # near iff eta > ETA_NS: every touching pair (eta >= 1) is near
 NEAR_N = 3                      # Gauss-Legendre nodes per collapsed direction
 NEAR_K = 1                      # uniform refinements of the target element
+ETA0 = 0.5                      # box neighbours: eta = sqrt3/|o| > ETA0 (Sec. 5 value; 0.9: the 27 touching boxes)
 
 
 def build_lib(force: bool = False) -> str:
@@ -60,7 +61,7 @@ def lib():
             L.orc_tri_quad.argtypes = [p, i64, p, p]
             L.orc_direct.argtypes = [i, p, i64, p, i64, p, i, p, i64, d, p, p, i, i, p, i]
             L.orc_fmm.restype = i
-            L.orc_fmm.argtypes = [i, p, i64, p, i64, p, i, i, i, d, p, p, i, i, p, i64, p, p, i, p]
+            L.orc_fmm.argtypes = [i, p, i64, p, i64, p, i, i, i, d, d, p, p, i, i, p, i64, p, p, i, p]
             L.orc_taylor_b.argtypes = [p, i, p]
             L.orc_m2l_matrix.argtypes = [p, i, p]
             L.orc_p2m.argtypes = [p, p, i64, p, i, p]
@@ -170,7 +171,8 @@ def direct(task: str, mesh, dens, targets=None, eta_ns: float = ETA_NS, n: int =
     return out
 
 
-def fmm(task: str, mesh, dens, p: int = 4, leaf_size: int = 64, targets=None, eta_ns: float = ETA_NS,
+def fmm(task: str, mesh, dens, p: int = 4, leaf_size: int = 64, targets=None, eta0: float = ETA0,
+        eta_ns: float = ETA_NS,
         n: int = NEAR_N, k: int = NEAR_K, nthreads: int = 0, return_stats: bool = False):
     """O2: the FP64 reference FMM; returns u[d, t] (and tree statistics)."""
     tets, tris, tgt, src = _task_arrays(task, mesh)
@@ -182,7 +184,7 @@ def fmm(task: str, mesh, dens, p: int = 4, leaf_size: int = 64, targets=None, et
     st = np.zeros(8, np.int64)
     gx, gw = gauss_legendre01(n)
     lib().orc_fmm(TASKS[task], _ptr(tets), tets.shape[0], _ptr(tris), tris.shape[0], _ptr(dens),
-                  dens.shape[0], p, leaf_size, eta_ns, _ptr(gx), _ptr(gw), n, k, _ptr(targets),
+                  dens.shape[0], p, leaf_size, eta0, eta_ns, _ptr(gx), _ptr(gw), n, k, _ptr(targets),
                   targets.size, _ptr(out), _ptr(raw), nthreads, _ptr(st))
     if return_stats:
         keys = ["nbox", "nleaf", "maxlevel", "n_m2l", "n_p2p"]

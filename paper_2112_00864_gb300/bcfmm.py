@@ -27,7 +27,7 @@ EXPORTED = ["bcfmm_default_params", "bcfmm_build_bc_tree", "bcfmm_set_density", 
 
 class Params(C.Structure):
     _fields_ = [("p", C.c_int32), ("leaf_size", C.c_int32), ("eta_ns", C.c_double), ("near_n", C.c_int32),
-                ("near_k", C.c_int32), ("precision", C.c_int32), ("timing", C.c_int32)]
+                ("near_k", C.c_int32), ("precision", C.c_int32), ("timing", C.c_int32), ("eta0", C.c_double)]
 
 
 class BcfmmError(RuntimeError):

@@ -76,7 +76,7 @@ struct bcfmm_ctx {
   int device = 0;
   cudaStream_t st = nullptr;
   bcfmm_params prm{};
-  int np = 0;
+  int np = 0, ncode = 0;
   int nlevels = 0, nbox = 0, nleaf = 0;
   int64_t ntet = 0, ntri = 0, npts[2] = {0, 0};
   DevAlloc mem;
@@ -96,9 +96,10 @@ struct bcfmm_ctx {
   // stats
   double sec_setup = 0, sec_tree = 0, sec_lists = 0, sec_near_host = 0, sec_near_dev = 0;
   std::vector<int> leaves_per_level, boxes_per_level;
-  float stage_ms[8] = {0};
-  cudaEvent_t ev[9] = {};
-  bool ev_ok = false;
+  // per task: CUDA events around the stages of the last evaluation; elapsed
+  // times are read lazily by bcfmm_stats (no host sync inside an eval)
+  cudaEvent_t ev[3][8] = {};
+  bool ev_ok = false, ev_rec[3] = {false, false, false};
 };
 
 static double wall() {
@@ -120,6 +121,7 @@ extern "C" void bcfmm_default_params(bcfmm_params* prm) {
   prm->near_k = 1;
   prm->precision = BCFMM_FP64;
   prm->timing = 0;
+  prm->eta0 = 0.5;
 }
 
 extern "C" const char* bcfmm_last_error(void) { return g_err.c_str(); }
@@ -145,6 +147,14 @@ static int upload_task(bcfmm_ctx* C, const HostSetup& H, int t) {
   CU(m.upload(&near_off, T.near_off.data(), T.near_off.size(), st));
   CU(m.upload(&near_box, T.near_box.data(), T.near_box.size(), st));
   L.p2p_leaf = p2p_leaf; L.near_off = near_off; L.near_box = near_box;
+  {
+    int *run_off, *self_len;
+    int2* runs;
+    CU(m.upload(&run_off, T.run_off.data(), T.run_off.size(), st));
+    CU(m.upload(&self_len, T.self_len.data(), T.self_len.size(), st));
+    CU(m.upload(&runs, reinterpret_cast<const int2*>(T.runs.data()), T.runs.size() / 2, st));
+    L.run_off = run_off; L.runs = runs; L.self_len = self_len;
+  }
   L.n_m2l = (int)T.m2l_tgt.size();
   CU(m.upload(&m2l_tgt, T.m2l_tgt.data(), T.m2l_tgt.size(), st));
   CU(m.upload(&vl_off, T.vl_off.data(), T.vl_off.size(), st));
@@ -245,6 +255,7 @@ static int build_impl(const double* verts, int64_t nvert, const int32_t* tets, i
   if (prm.p < 0 || prm.p > kMaxP) return fail(BCFMM_ERR_ARG, "build_bc_tree: p must be in 0..12");
   if (prm.leaf_size < 1 || prm.leaf_size > 128) return fail(BCFMM_ERR_ARG, "build_bc_tree: leaf_size must be in 1..128");
   if (!(prm.eta_ns > 0)) return fail(BCFMM_ERR_ARG, "build_bc_tree: eta_ns must be > 0");
+  if (!(prm.eta0 >= 0.3 && prm.eta0 <= 1.0)) return fail(BCFMM_ERR_ARG, "build_bc_tree: eta0 must be in 0.3..1");
   if (prm.near_n < 1 || prm.near_n > 8 || prm.near_k < 0 || prm.near_k > 3)
     return fail(BCFMM_ERR_ARG, "build_bc_tree: near_n must be in 1..8 and near_k in 0..3");
   if (prm.precision < BCFMM_FP64 || prm.precision > BCFMM_FP32_BF16X3)
@@ -271,7 +282,8 @@ static int build_impl(const double* verts, int64_t nvert, const int32_t* tets, i
   for (auto& B : H.box)
     if (!B.nchild && (B.pt1[0] - B.pt0[0] > 128 || B.pt1[1] - B.pt0[1] > 128))
       return cleanup(fail(BCFMM_ERR_MESH, "build_bc_tree: more than 128 coincident points in one leaf at the deepest level"));
-  build_lists(H);
+  build_lists(H, prm.eta0);
+  if (H.offsets.size() / 3 > 65535) return cleanup(fail(BCFMM_ERR_ARG, "build_bc_tree: too many interaction offsets"));
   find_near_pairs(H, prm.eta_ns);
   C->sec_tree = H.seconds_tree;
   C->sec_lists = H.seconds_lists;
@@ -347,11 +359,11 @@ static int build_impl(const double* verts, int64_t nvert, const int32_t* tets, i
   // translation tables: M2L transposed per offset code, M2M / L2L per octant
   {
     const int np = C->np;
-    std::vector<double> T(kNumOffsets * (size_t)np * np, 0.0), Tt(kNumOffsets * (size_t)np * np, 0.0), tmp(np * np);
-    for (int code = 0; code < kNumOffsets; ++code) {
-      int o[3] = {code % 7 - 3, (code / 7) % 7 - 3, code / 49 - 3};
-      if (std::abs(o[0]) <= 1 && std::abs(o[1]) <= 1 && std::abs(o[2]) <= 1) continue;
-      double od[3] = {(double)o[0], (double)o[1], (double)o[2]};
+    const int ncode = (int)(H.offsets.size() / 3);
+    C->ncode = ncode;
+    std::vector<double> T((size_t)std::max(ncode, 1) * np * np, 0.0), Tt(T.size(), 0.0), tmp(np * np);
+    for (int code = 0; code < ncode; ++code) {
+      double od[3] = {(double)H.offsets[3 * code], (double)H.offsets[3 * code + 1], (double)H.offsets[3 * code + 2]};
       m2l_matrix_scaled(prm.p, od, tmp.data());
       for (int a = 0; a < np; ++a)
         for (int b = 0; b < np; ++b) {
@@ -359,9 +371,16 @@ static int build_impl(const double* verts, int64_t nvert, const int32_t* tets, i
           Tt[((size_t)code * np + b) * np + a] = tmp[a * np + b];
         }
     }
-    std::vector<double> Mm, Lm;
-    m2m_matrices(prm.p, Mm);
-    l2l_matrices(prm.p, Lm);
+    std::vector<double> Mm0, Lm0;
+    m2m_matrices(prm.p, Mm0);
+    l2l_matrices(prm.p, Lm0);
+    std::vector<double> Mm(Mm0.size()), Lm(Lm0.size());   // transposed per octant
+    for (int q = 0; q < 8; ++q)
+      for (int a = 0; a < np; ++a)
+        for (int b = 0; b < np; ++b) {
+          Mm[((size_t)q * np + b) * np + a] = Mm0[((size_t)q * np + a) * np + b];
+          Lm[((size_t)q * np + b) * np + a] = Lm0[((size_t)q * np + a) * np + b];
+        }
     std::vector<float> Tt32(Tt.begin(), Tt.end()), M32(Mm.begin(), Mm.end()), L32(Lm.begin(), Lm.end());
     bool ok = m.upload(&C->T64, Tt.data(), Tt.size(), st) == cudaSuccess &&
               m.upload(&C->M2M64, Mm.data(), Mm.size(), st) == cudaSuccess &&
@@ -371,7 +390,7 @@ static int build_impl(const double* verts, int64_t nvert, const int32_t* tets, i
               m.upload(&C->L2L32, L32.data(), L32.size(), st) == cudaSuccess;
     if (!ok) return cleanup(fail(BCFMM_ERR_OOM, "build_bc_tree: device allocation failed (tables)"));
     if (prm.precision == BCFMM_FP32_BF16X2 || prm.precision == BCFMM_FP32_BF16X3) {
-      cudaError_t ce = m2l_tc_prepare_tables(prm.p, T.data(), prm.precision == BCFMM_FP32_BF16X3 ? 3 : 2, &C->tc, st);
+      cudaError_t ce = m2l_tc_prepare_tables(prm.p, ncode, T.data(), prm.precision == BCFMM_FP32_BF16X3 ? 3 : 2, &C->tc, st);
       if (ce != cudaSuccess) return cleanup(fail(BCFMM_ERR_CUDA, std::string("build_bc_tree: tensor tables: ") + cudaGetErrorString(ce)));
     }
   }
@@ -384,7 +403,9 @@ static int build_impl(const double* verts, int64_t nvert, const int32_t* tets, i
   if (cudaStreamSynchronize(st) != cudaSuccess) return cleanup(fail(BCFMM_ERR_CUDA, "build_bc_tree: stream sync failed"));
   if (prm.timing) {
     C->ev_ok = true;
-    for (auto& ev : C->ev) if (cudaEventCreate(&ev) != cudaSuccess) C->ev_ok = false;
+    for (auto& row : C->ev)
+      for (auto& ev : row)
+        if (cudaEventCreate(&ev) != cudaSuccess) C->ev_ok = false;
   }
   C->sec_setup = wall() - t0;
   *out = C;
@@ -454,12 +475,13 @@ extern "C" int bcfmm_set_density(bcfmm_ctx* C, int32_t kind, const double* vals,
 }
 
 static int eval_impl(bcfmm_ctx* C, int t, double* out, int out_is_device) {
-  if (!C || !out) return fail(BCFMM_ERR_ARG, "eval: null argument");
+  if (!C) return fail(BCFMM_ERR_ARG, "eval: null context");
   TaskDev& D = C->task[t];
   const DevTaskLists& L = D.L;
   const int kind = L.src_cls;     // class 0 sources: volume density; class 1: boundary density
   if (C->ndens[kind] == 0)
     return fail(BCFMM_ERR_STATE, kind == 0 ? "eval: volume density not set" : "eval: boundary density not set");
+  if (!out) return fail(BCFMM_ERR_ARG, "eval: null output");
   const int ndens = C->ndens[kind], ndp = C->ndp[kind];
   const int rc = ensure_work(C, ndp);
   if (rc != BCFMM_OK) return rc;
@@ -471,59 +493,57 @@ static int eval_impl(bcfmm_ctx* C, int t, double* out, int out_is_device) {
   const bool f64 = C->prm.precision == BCFMM_FP64;
   const bool tc = C->prm.precision == BCFMM_FP32_BF16X2 || C->prm.precision == BCFMM_FP32_BF16X3;
   const bool tm = C->prm.timing && C->ev_ok;
+  cudaEvent_t* ev = C->ev[t];
   double* outd = out_is_device ? out : C->out_dev;
-  if (tm) CU(cudaEventRecord(C->ev[0], st));
+  if (tm) CU(cudaEventRecord(ev[0], st));
   if (f64) {
     CU(launch_weights<double>(G, L.src_cls, nsp, C->dens[kind], nsel, ndens, ndp, C->W64, st));
     CU(cudaMemsetAsync(C->mom64, 0, nexp * sizeof(double), st));
     CU(cudaMemsetAsync(C->loc64, 0, nexp * sizeof(double), st));
-    if (tm) CU(cudaEventRecord(C->ev[1], st));
+    if (tm) CU(cudaEventRecord(ev[1], st));
     CU(launch_p2m<double>(G, L, C->W64, nsp, ndp, C->mom64, st));
     for (int l = C->nlevels - 1; l >= 0; --l) {
       const int n = D.m2m_off[l + 1] - D.m2m_off[l];
       CU(launch_m2m<double>(G, D.m2m_parent + D.m2m_off[l], n, C->M2M64, ndp, C->mom64, st));
     }
-    if (tm) CU(cudaEventRecord(C->ev[2], st));
+    if (tm) CU(cudaEventRecord(ev[2], st));
     CU(launch_m2l_simt<double>(G, L, C->T64, G.tri_k, ndp, C->mom64, C->loc64, st));
-    if (tm) CU(cudaEventRecord(C->ev[3], st));
+    if (tm) CU(cudaEventRecord(ev[3], st));
     for (int l = 3; l < C->nlevels; ++l) {
       const int n = D.l2l_off[l + 1] - D.l2l_off[l];
       CU(launch_l2l<double>(G, D.l2l_child + D.l2l_off[l], n, C->L2L64, ndp, C->loc64, st));
     }
-    if (tm) CU(cudaEventRecord(C->ev[4], st));
+    if (tm) CU(cudaEventRecord(ev[4], st));
     CU(launch_p2p_l2p_f64(G, L, C->W64, nsp, ntp, ndp, C->loc64, C->phi, st));
   } else {
     CU(launch_weights<float>(G, L.src_cls, nsp, C->dens[kind], nsel, ndens, ndp, C->W32, st));
     CU(cudaMemsetAsync(C->mom32, 0, nexp * sizeof(float), st));
     CU(cudaMemsetAsync(C->loc32, 0, nexp * sizeof(float), st));
-    if (tm) CU(cudaEventRecord(C->ev[1], st));
+    if (tm) CU(cudaEventRecord(ev[1], st));
     CU(launch_p2m<float>(G, L, C->W32, nsp, ndp, C->mom32, st));
     for (int l = C->nlevels - 1; l >= 0; --l) {
       const int n = D.m2m_off[l + 1] - D.m2m_off[l];
       CU(launch_m2m<float>(G, D.m2m_parent + D.m2m_off[l], n, C->M2M32, ndp, C->mom32, st));
     }
-    if (tm) CU(cudaEventRecord(C->ev[2], st));
+    if (tm) CU(cudaEventRecord(ev[2], st));
     if (tc) CU(launch_m2l_tc(G, L, C->tc, ndp, C->mom32, C->loc32, st));
     else CU(launch_m2l_simt<float>(G, L, C->T32, G.tri_k, ndp, C->mom32, C->loc32, st));
-    if (tm) CU(cudaEventRecord(C->ev[3], st));
+    if (tm) CU(cudaEventRecord(ev[3], st));
     for (int l = 3; l < C->nlevels; ++l) {
       const int n = D.l2l_off[l + 1] - D.l2l_off[l];
       CU(launch_l2l<float>(G, D.l2l_child + D.l2l_off[l], n, C->L2L32, ndp, C->loc32, st));
     }
-    if (tm) CU(cudaEventRecord(C->ev[4], st));
+    if (tm) CU(cudaEventRecord(ev[4], st));
     CU(launch_p2p_l2p_f32(G, L, C->W32, nsp, ntp, ndp, C->loc32, C->phi, st));
   }
-  if (tm) CU(cudaEventRecord(C->ev[5], st));
+  if (tm) CU(cudaEventRecord(ev[5], st));
   CU(launch_elem_sum(G, L, C->phi, ntp, C->dens[kind], ndens, outd, st));
-  if (tm) CU(cudaEventRecord(C->ev[6], st));
+  if (tm) CU(cudaEventRecord(ev[6], st));
   if (!out_is_device) {
     CU(cudaMemcpyAsync(out, C->out_dev, (size_t)ndens * L.ntgt_el * sizeof(double), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
   }
-  if (tm) {
-    CU(cudaEventSynchronize(C->ev[6]));
-    for (int i = 0; i < 6; ++i) CU(cudaEventElapsedTime(&C->stage_ms[i], C->ev[i], C->ev[i + 1]));
-  }
+  C->ev_rec[t] = tm;
   return BCFMM_OK;
 }
 
@@ -541,7 +561,7 @@ extern "C" int bcfmm_stats(const bcfmm_ctx* C, char* json, size_t cap) {
   };
   kv("ntet", (double)C->ntet); kv("ntri", (double)C->ntri);
   kv("npts_tet", (double)C->npts[0]); kv("npts_tri", (double)C->npts[1]);
-  kv("p", C->prm.p); kv("np", C->np); kv("leaf_size", C->prm.leaf_size); kv("precision", C->prm.precision);
+  kv("p", C->prm.p); kv("np", C->np); kv("eta0", C->prm.eta0); kv("n_offsets", C->ncode); kv("leaf_size", C->prm.leaf_size); kv("precision", C->prm.precision);
   kv("nbox", C->nbox); kv("nleaf", C->nleaf); kv("nlevels", C->nlevels);
   kv("setup_s", C->sec_setup); kv("tree_s", C->sec_tree); kv("lists_s", C->sec_lists);
   kv("near_search_s", C->sec_near_host); kv("near_rule_s", C->sec_near_dev);
@@ -556,9 +576,21 @@ extern "C" int bcfmm_stats(const bcfmm_ctx* C, char* json, size_t cap) {
              C->task[t].L.n_p2m);
     s += b;
   }
-  s += "\"stage_ms\": [";
-  for (int i = 0; i < 6; ++i) { char b[32]; snprintf(b, sizeof b, "%.6g%s", C->stage_ms[i], i < 5 ? ", " : ""); s += b; }
-  s += "], \"leaves_per_level\": [";
+  // stages: weights+clear, P2M+M2M, M2L, L2L, L2P+P2P, element sums+corrections
+  s += "\"stage_ms\": {";
+  for (int t = 0; t < 3; ++t) {
+    s += std::string("\"") + names[t] + "\": [";
+    for (int i = 0; i < 6; ++i) {
+      float ms = -1.f;
+      if (C->ev_rec[t] && cudaEventSynchronize(C->ev[t][6]) == cudaSuccess)
+        cudaEventElapsedTime(&ms, C->ev[t][i], C->ev[t][i + 1]);
+      char b[32];
+      snprintf(b, sizeof b, "%.6g%s", ms, i < 5 ? ", " : "");
+      s += b;
+    }
+    s += t < 2 ? "], " : "]";
+  }
+  s += "}, \"leaves_per_level\": [";
   for (size_t i = 0; i < C->leaves_per_level.size(); ++i) s += std::to_string(C->leaves_per_level[i]) + (i + 1 < C->leaves_per_level.size() ? ", " : "");
   s += "], \"boxes_per_level\": [";
   for (size_t i = 0; i < C->boxes_per_level.size(); ++i) s += std::to_string(C->boxes_per_level[i]) + (i + 1 < C->boxes_per_level.size() ? ", " : "");
@@ -571,7 +603,9 @@ extern "C" int bcfmm_stats(const bcfmm_ctx* C, char* json, size_t cap) {
 extern "C" void bcfmm_destroy(bcfmm_ctx* C) {
   if (!C) return;
   cudaStreamSynchronize(C->st);
-  if (C->ev_ok) for (auto& ev : C->ev) cudaEventDestroy(ev);
+  if (C->ev_ok)
+    for (auto& row : C->ev)
+      for (auto& ev : row) cudaEventDestroy(ev);
   m2l_tc_free_tables(&C->tc);
   C->mem.free_all();
   delete C;

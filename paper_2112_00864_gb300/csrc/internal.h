@@ -9,7 +9,6 @@ namespace bcfmm {
 constexpr double kFourPi = 12.566370614359172953850573533118;
 constexpr int kMaxLevel = 18;
 constexpr int kMaxP = 12;
-constexpr int kNumOffsets = 343;   // o in [-3,3]^3, code = (ox+3) + 7 (oy+3) + 49 (oz+3)
 
 inline int nterms(int p) { return (p + 1) * (p + 2) * (p + 3) / 6; }
 
@@ -41,6 +40,7 @@ struct HostTask {
   int src_cls = 0, tgt_cls = 0;
   // P2P: target leaves and their extended neighbour list N* as box ids
   std::vector<int> p2p_leaf, near_off, near_box;
+  std::vector<int> run_off, runs, self_len;        // merged source runs (start, end) per target leaf
   // M2L: target boxes (level >= 2 with target points) and interaction lists
   std::vector<int> m2l_tgt, vl_off, vl_src;
   std::vector<uint16_t> vl_code;
@@ -68,6 +68,7 @@ struct HostSetup {
   std::vector<int> perm[2];                        // sorted position -> original point index
   std::vector<int> leaf_of[2];                     // sorted position -> leaf box
   HostTask task[3];
+  std::vector<int> offsets;                        // distinct interaction offsets (x,y,z) per code
   double seconds_tree = 0, seconds_lists = 0, seconds_near = 0;
 };
 
@@ -77,14 +78,14 @@ struct HostSetup {
 std::string setup_mesh(HostSetup& H, const double* verts, int64_t nvert, const int32_t* tets,
                        int64_t ntet, const int32_t* tris, int64_t ntri, bool* mesh_err);
 void build_tree(HostSetup& H, int leaf_size);
-void build_lists(HostSetup& H);
+void build_lists(HostSetup& H, double eta0);
 void find_near_pairs(HostSetup& H, double eta_ns);
 
 // Gauss-Legendre nodes/weights on [0,1] (Newton iteration on P_n).
 void gauss_legendre01(int n, std::vector<double>& x, std::vector<double>& w);
 
 // Box-scaled translation tables (Sec. 3.3).
-//  M2L: T[code][a][b] for all 343 offset codes (zero for |o|_inf <= 1).
+//  M2L: T[a][b] for one offset o (in box units).
 //  M2M: for child octant q, m_parent[b] += sum_g M[q][b][g] m_child[g].
 //  L2L: for child octant q, l_child[a] += sum_b L[q][a][b] l_parent[b].
 void m2l_matrix_scaled(int p, const double o[3], double* T);

@@ -26,6 +26,7 @@ struct DevGeom {
 
 struct DevTaskLists {
   int n_p2p; const int* p2p_leaf; const int* near_off; const int* near_box;
+  const int* run_off; const int2* runs; const int* self_len;   // merged source runs per target leaf
   int n_m2l; const int* m2l_tgt; const int* vl_off; const int* vl_src; const uint16_t* vl_code;
   int n_p2m; const int* p2m_leaf;
   int n_l2p; const int* l2p_leaf;

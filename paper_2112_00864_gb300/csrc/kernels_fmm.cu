@@ -87,7 +87,8 @@ cudaError_t launch_p2m(const DevGeom& G, const DevTaskLists& L, const T* W, int6
 }
 
 // ---------------------------------------------------------------- M2M
-// m_parent[b] = sum_children sum_g M[octant][b][g] m_child[g]
+// m_parent[b] = sum_children sum_g M[octant][b][g] m_child[g]; the table is
+// stored transposed, Mt[octant][g][b], so threads (b) read it coalesced.
 template <typename T>
 __global__ void k_m2m(DevGeom G, const int* __restrict__ parents, const T* __restrict__ M2M, int ndp,
                       T* __restrict__ mom) {
@@ -106,8 +107,8 @@ __global__ void k_m2m(DevGeom G, const int* __restrict__ parents, const T* __res
     for (int b = threadIdx.x; b < np; b += blockDim.x) {
       T acc = 0;
       for (int c = 0; c < nc; ++c) {
-        const T* Mr = M2M + ((int64_t)G.box_octant[c0 + c] * np + b) * np;
-        for (int g = 0; g <= b; ++g) acc += Mr[g] * mc[c * np + g];   // g <= b: lower degree first
+        const T* Mt = M2M + (int64_t)G.box_octant[c0 + c] * np * np;
+        for (int g = 0; g <= b; ++g) acc += Mt[(int64_t)g * np + b] * mc[c * np + g];   // g <= b
       }
       mom[((int64_t)P * ndp + d) * np + b] = acc;
     }
@@ -134,9 +135,11 @@ __global__ void k_m2l_simt(DevGeom G, DevTaskLists L, const T* __restrict__ Tt, 
   const int tb = L.m2l_tgt[blockIdx.x];
   const int a = threadIdx.x;
   const int K = (a < np) ? G.tri_k[a] : 0;
-  T acc[ND];
+  // products of one translation in T, the sum over the interaction list
+  // (~10^3 entries for eta0 = 0.5) in FP64
+  double acc[ND];
 #pragma unroll
-  for (int d = 0; d < ND; ++d) acc[d] = 0;
+  for (int d = 0; d < ND; ++d) acc[d] = 0.0;
   const int e0 = L.vl_off[blockIdx.x], e1 = L.vl_off[blockIdx.x + 1];
   for (int e = e0; e < e1; ++e) {
     const int sb = L.vl_src[e];
@@ -145,17 +148,22 @@ __global__ void k_m2l_simt(DevGeom G, DevTaskLists L, const T* __restrict__ Tt, 
     for (int i = threadIdx.x; i < ND * np; i += blockDim.x) ms[i] = mom[(int64_t)sb * ndp * np + i];
     __syncthreads();
     if (a < np) {
+      T part[ND];
+#pragma unroll
+      for (int d = 0; d < ND; ++d) part[d] = 0;
       for (int b = 0; b < K; ++b) {
         const T t = Tc[(int64_t)b * np + a];
 #pragma unroll
-        for (int d = 0; d < ND; ++d) acc[d] += t * ms[d * np + b];
+        for (int d = 0; d < ND; ++d) part[d] += t * ms[d * np + b];
       }
+#pragma unroll
+      for (int d = 0; d < ND; ++d) acc[d] += (double)part[d];
     }
   }
   if (a < np) {
-    const T inv_s = (T)(1.0 / G.box_cs[tb].w);
+    const double inv_s = 1.0 / G.box_cs[tb].w;
 #pragma unroll
-    for (int d = 0; d < ND; ++d) loc[((int64_t)tb * ndp + d) * np + a] = acc[d] * inv_s;
+    for (int d = 0; d < ND; ++d) loc[((int64_t)tb * ndp + d) * np + a] = (T)(acc[d] * inv_s);
   }
 }
 
@@ -177,7 +185,8 @@ cudaError_t launch_m2l_simt(const DevGeom& G, const DevTaskLists& L, const T* Tt
 }
 
 // ---------------------------------------------------------------- L2L
-// l_child[a] += sum_{b >= a} L[octant][a][b] l_parent[b]
+// l_child[a] += sum_{b >= a} L[octant][a][b] l_parent[b]; stored transposed,
+// Lt[octant][b][a], for coalesced reads over a.
 template <typename T>
 __global__ void k_l2l(DevGeom G, const int* __restrict__ children, const T* __restrict__ L2L, int ndp,
                       T* __restrict__ loc) {
@@ -193,8 +202,7 @@ __global__ void k_l2l(DevGeom G, const int* __restrict__ children, const T* __re
     __syncthreads();
     for (int a = threadIdx.x; a < np; a += blockDim.x) {
       T acc = 0;
-      const T* Lr = Lm + (int64_t)a * np;
-      for (int b = a; b < np; ++b) acc += Lr[b] * lp[b];
+      for (int b = a; b < np; ++b) acc += Lm[(int64_t)b * np + a] * lp[b];
       loc[((int64_t)C * ndp + d) * np + a] += acc;
     }
   }
@@ -210,32 +218,92 @@ cudaError_t launch_l2l(const DevGeom& G, const int* children, int n, const T* L2
 // ------------------------------------------------ evaluation + near field
 // One CTA (128 threads) per target leaf.  Targets are padded to TP in
 // {32, 64, 128}; the 128/TP thread groups split each source tile and are
-// reduced at the end.  Source tiles are staged in shared memory, translated
-// to the target leaf's frame with double-float (hi + lo) arithmetic so that
-// FP32 differences keep full relative accuracy.  The self point (r == 0) is
-// skipped.  FP32 partial sums are folded into FP64 once per source box.
+// reduced at the end.  The sources of N* arrive as merged runs of the sorted
+// point array and are streamed through shared memory in tiles that span
+// run boundaries.  FP32 coordinates are translated to the target leaf's
+// frame with double-float (hi + lo) arithmetic, so differences keep full
+// relative accuracy.  Only the leaf's own run (first, VtV) can hold the
+// target point itself; tiles overlapping it skip r == 0.  FP32 partial sums
+// are folded into FP64 once per tile.
 constexpr int kTile = 256;
+constexpr int kRunBatch = 256;
 
 __device__ __forceinline__ void split_df(double v, float& hi, float& lo) {
   hi = (float)v;
   lo = (float)(v - (double)hi);
 }
 
+// largest r in [0, n) with pre[r] <= v  (pre[0] = 0 <= v < pre[n])
+__device__ __forceinline__ int find_run(const int* pre, int n, int v) {
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (pre[mid] <= v) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// prefix sums of the run lengths of one batch (warp 0), starts into rst
+__device__ __forceinline__ void scan_runs(const int2* __restrict__ runs, int nr, int* pre, int* rst) {
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    int carry = 0;
+    if (lane == 0) pre[0] = 0;
+    for (int c = 0; c < nr; c += 32) {
+      const int r = c + lane;
+      int len = 0;
+      if (r < nr) { const int2 rr = runs[r]; len = rr.y - rr.x; rst[r] = rr.x; }
+      int x = len;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) { const int y = __shfl_up_sync(0xffffffffu, x, o); if (lane >= o) x += y; }
+      if (r < nr) pre[r + 1] = carry + x;
+      carry += __shfl_sync(0xffffffffu, x, 31);
+    }
+  }
+}
+
+template <typename T, int ND>
+__device__ __forceinline__ void l2p_and_store(const DevGeom& G, int leaf, int ndp, const T* __restrict__ loc,
+                                              double xs, double ys, double zs, const double* near, int64_t pos,
+                                              int64_t ntp, double* __restrict__ phi) {
+  double far[ND];
+#pragma unroll
+  for (int d = 0; d < ND; ++d) far[d] = 0.0;
+  // L2P: phi_far(x) = sum_a l^a xhat^a, xhat = (x - c)/s (locals of boxes
+  // without an interaction list are zero)
+  if (loc != nullptr) {
+    T px[16], py[16], pz[16];
+    px[0] = py[0] = pz[0] = (T)1;
+    for (int k = 1; k <= G.p; ++k) { px[k] = px[k - 1] * (T)xs; py[k] = py[k - 1] * (T)ys; pz[k] = pz[k - 1] * (T)zs; }
+    const T* lb = loc + (int64_t)leaf * ndp * G.np;
+    for (int q = 0; q < G.np; ++q) {
+      const int mi = G.mi[q];
+      const T mono = px[mi & 255] * py[(mi >> 8) & 255] * pz[(mi >> 16) & 255];
+#pragma unroll
+      for (int d = 0; d < ND; ++d) far[d] += (double)(lb[d * G.np + q] * mono);
+    }
+  }
+#pragma unroll
+  for (int d = 0; d < ND; ++d) phi[(int64_t)d * ntp + pos] = near[d] * kInv4Pi + far[d];
+}
+
 template <int ND>
 __global__ void __launch_bounds__(128) k_p2p_l2p_f32(DevGeom G, DevTaskLists L, const float* __restrict__ W,
                                                      int64_t nsp, int64_t ntp, int ndp,
                                                      const float* __restrict__ loc, double* __restrict__ phi) {
-  __shared__ float sx[kTile], sy[kTile], sz[kTile];
-  __shared__ float sw[ND][kTile];
+  __shared__ float4 tile[kTile];
+  __shared__ float tw[ND > 1 ? ND - 1 : 1][kTile];
+  __shared__ int pre[kRunBatch + 1], rst[kRunBatch];
   __shared__ double red[ND][128];
-  const int leaf = L.p2p_leaf[blockIdx.x];
+  const int b = blockIdx.x;
+  const int leaf = L.p2p_leaf[b];
   const int sc = L.src_cls, tc = L.tgt_cls;
   const double4_32a cs = G.box_cs[leaf];
   float chx, clx, chy, cly, chz, clz;
   split_df(cs.x, chx, clx); split_df(cs.y, chy, cly); split_df(cs.z, chz, clz);
   const int2 tr = G.box_rng[tc][leaf];
   const int nt = tr.y - tr.x;
-  const int TP = nt <= 32 ? 32 : (nt <= 64 ? 64 : 128);
+  const int TP = nt <= 8 ? 8 : (nt <= 16 ? 16 : (nt <= 32 ? 32 : (nt <= 64 ? 64 : 128)));
   const int NG = 128 / TP;
   const int ti = threadIdx.x % TP, gi = threadIdx.x / TP;
   const bool active = ti < nt;
@@ -247,68 +315,73 @@ __global__ void __launch_bounds__(128) k_p2p_l2p_f32(DevGeom G, DevTaskLists L, 
     zt = (h.z - chz) + (l.z - clz);
   }
   double accd[ND];
-  float acc[ND];
 #pragma unroll
-  for (int d = 0; d < ND; ++d) { accd[d] = 0.0; acc[d] = 0.f; }
-  const int n0 = L.near_off[blockIdx.x], n1 = L.near_off[blockIdx.x + 1];
-  for (int nb = n0; nb < n1; ++nb) {
-    const int2 sr = G.box_rng[sc][L.near_box[nb]];
-    for (int j0 = sr.x; j0 < sr.y; j0 += kTile) {
-      const int m = min(kTile, sr.y - j0);
+  for (int d = 0; d < ND; ++d) accd[d] = 0.0;
+  const int r0 = L.run_off[b], r1 = L.run_off[b + 1];
+  const int self_len = L.self_len[b];
+  for (int rb = r0; rb < r1; rb += kRunBatch) {
+    const int nr = min(kRunBatch, r1 - rb);
+    __syncthreads();
+    scan_runs(L.runs + rb, nr, pre, rst);
+    __syncthreads();
+    const int total = pre[nr];
+    for (int j0 = 0; j0 < total; j0 += kTile) {
+      const int m = min(kTile, total - j0);
       __syncthreads();
       for (int j = threadIdx.x; j < m; j += 128) {
-        const float4 h = G.pthi[sc][j0 + j], l = G.ptlo[sc][j0 + j];
-        sx[j] = (h.x - chx) + (l.x - clx);
-        sy[j] = (h.y - chy) + (l.y - cly);
-        sz[j] = (h.z - chz) + (l.z - clz);
+        const int v = j0 + j;
+        const int r = find_run(pre, nr, v);
+        const int src = rst[r] + (v - pre[r]);
+        const float4 h = G.pthi[sc][src], l = G.ptlo[sc][src];
+        tile[j] = make_float4((h.x - chx) + (l.x - clx), (h.y - chy) + (l.y - cly), (h.z - chz) + (l.z - clz), W[src]);
 #pragma unroll
-        for (int d = 0; d < ND; ++d) sw[d][j] = W[(int64_t)d * nsp + j0 + j];
+        for (int d = 1; d < ND; ++d) tw[d - 1][j] = W[(int64_t)d * nsp + src];
       }
       __syncthreads();
       if (active) {
-#pragma unroll 4
-        for (int j = gi; j < m; j += NG) {
-          const float dx = xt - sx[j], dy = yt - sy[j], dz = zt - sz[j];
-          const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-          const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+        float acc[ND];
 #pragma unroll
-          for (int d = 0; d < ND; ++d) acc[d] = fmaf(sw[d][j], rinv, acc[d]);
+        for (int d = 0; d < ND; ++d) acc[d] = 0.f;
+        if (rb == r0 && j0 < self_len) {
+          for (int j = gi; j < m; j += NG) {
+            const float4 s = tile[j];
+            const float dx = xt - s.x, dy = yt - s.y, dz = zt - s.z;
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float ri = r2 > 0.f ? rsqrtf(r2) : 0.f;
+            acc[0] = fmaf(s.w, ri, acc[0]);
+#pragma unroll
+            for (int d = 1; d < ND; ++d) acc[d] = fmaf(tw[d - 1][j], ri, acc[d]);
+          }
+        } else {
+#pragma unroll 4
+          for (int j = gi; j < m; j += NG) {
+            const float4 s = tile[j];
+            const float dx = xt - s.x, dy = yt - s.y, dz = zt - s.z;
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float ri = rsqrtf(r2);
+            acc[0] = fmaf(s.w, ri, acc[0]);
+#pragma unroll
+            for (int d = 1; d < ND; ++d) acc[d] = fmaf(tw[d - 1][j], ri, acc[d]);
+          }
         }
+#pragma unroll
+        for (int d = 0; d < ND; ++d) accd[d] += (double)acc[d];
       }
     }
-#pragma unroll
-    for (int d = 0; d < ND; ++d) { accd[d] += (double)acc[d]; acc[d] = 0.f; }
   }
-  // reduce the NG source groups
 #pragma unroll
   for (int d = 0; d < ND; ++d) red[d][threadIdx.x] = accd[d];
   __syncthreads();
   if (gi == 0 && active) {
-    double far[ND];
-#pragma unroll
-    for (int d = 0; d < ND; ++d) far[d] = 0.0;
-    // L2P: phi_far(x) = sum_a l^a xhat^a, xhat = (x - c)/s (locals of boxes
-    // without an interaction list are zero)
-    if (loc != nullptr) {
-      const float inv_s = (float)(1.0 / cs.w);
-      const float xs = xt * inv_s, ys = yt * inv_s, zs = zt * inv_s;
-      float px[16], py[16], pz[16];
-      px[0] = py[0] = pz[0] = 1.f;
-      for (int k = 1; k <= G.p; ++k) { px[k] = px[k - 1] * xs; py[k] = py[k - 1] * ys; pz[k] = pz[k - 1] * zs; }
-      const float* lb = loc + (int64_t)leaf * ndp * G.np;
-      for (int q = 0; q < G.np; ++q) {
-        const int mi = G.mi[q];
-        const float mono = px[mi & 255] * py[(mi >> 8) & 255] * pz[(mi >> 16) & 255];
-#pragma unroll
-        for (int d = 0; d < ND; ++d) far[d] += (double)(lb[d * G.np + q] * mono);
-      }
-    }
+    double near[ND];
 #pragma unroll
     for (int d = 0; d < ND; ++d) {
       double s = 0.0;
       for (int g = 0; g < NG; ++g) s += red[d][g * TP + ti];
-      phi[(int64_t)d * ntp + tr.x + ti] = s * kInv4Pi + far[d];
+      near[d] = s;
     }
+    const double inv_s = 1.0 / cs.w;
+    l2p_and_store<float, ND>(G, leaf, ndp, loc, xt * inv_s, yt * inv_s, zt * inv_s, near, tr.x + ti, ntp, phi);
   }
 }
 
@@ -316,16 +389,18 @@ template <int ND>
 __global__ void __launch_bounds__(128) k_p2p_l2p_f64(DevGeom G, DevTaskLists L, const double* __restrict__ W,
                                                      int64_t nsp, int64_t ntp, int ndp,
                                                      const double* __restrict__ loc, double* __restrict__ phi) {
-  __shared__ double sx[kTile / 2], sy[kTile / 2], sz[kTile / 2];
-  __shared__ double sw[ND][kTile / 2];
-  __shared__ double red[ND][128];
   constexpr int TL = kTile / 2;
-  const int leaf = L.p2p_leaf[blockIdx.x];
+  __shared__ double4_32a tile[TL];
+  __shared__ double tw[ND > 1 ? ND - 1 : 1][TL];
+  __shared__ int pre[kRunBatch + 1], rst[kRunBatch];
+  __shared__ double red[ND][128];
+  const int b = blockIdx.x;
+  const int leaf = L.p2p_leaf[b];
   const int sc = L.src_cls, tc = L.tgt_cls;
   const double4_32a cs = G.box_cs[leaf];
   const int2 tr = G.box_rng[tc][leaf];
   const int nt = tr.y - tr.x;
-  const int TP = nt <= 32 ? 32 : (nt <= 64 ? 64 : 128);
+  const int TP = nt <= 8 ? 8 : (nt <= 16 ? 16 : (nt <= 32 ? 32 : (nt <= 64 ? 64 : 128)));
   const int NG = 128 / TP;
   const int ti = threadIdx.x % TP, gi = threadIdx.x / TP;
   const bool active = ti < nt;
@@ -337,26 +412,35 @@ __global__ void __launch_bounds__(128) k_p2p_l2p_f64(DevGeom G, DevTaskLists L, 
   double acc[ND];
 #pragma unroll
   for (int d = 0; d < ND; ++d) acc[d] = 0.0;
-  const int n0 = L.near_off[blockIdx.x], n1 = L.near_off[blockIdx.x + 1];
-  for (int nb = n0; nb < n1; ++nb) {
-    const int2 sr = G.box_rng[sc][L.near_box[nb]];
-    for (int j0 = sr.x; j0 < sr.y; j0 += TL) {
-      const int m = min(TL, sr.y - j0);
+  const int r0 = L.run_off[b], r1 = L.run_off[b + 1];
+  for (int rb = r0; rb < r1; rb += kRunBatch) {
+    const int nr = min(kRunBatch, r1 - rb);
+    __syncthreads();
+    scan_runs(L.runs + rb, nr, pre, rst);
+    __syncthreads();
+    const int total = pre[nr];
+    for (int j0 = 0; j0 < total; j0 += TL) {
+      const int m = min(TL, total - j0);
       __syncthreads();
       for (int j = threadIdx.x; j < m; j += 128) {
-        const double4_32a y = G.pt64[sc][j0 + j];
-        sx[j] = y.x; sy[j] = y.y; sz[j] = y.z;
+        const int v = j0 + j;
+        const int r = find_run(pre, nr, v);
+        const int src = rst[r] + (v - pre[r]);
+        const double4_32a y = G.pt64[sc][src];
+        tile[j] = make_double4_32a(y.x, y.y, y.z, W[src]);
 #pragma unroll
-        for (int d = 0; d < ND; ++d) sw[d][j] = W[(int64_t)d * nsp + j0 + j];
+        for (int d = 1; d < ND; ++d) tw[d - 1][j] = W[(int64_t)d * nsp + src];
       }
       __syncthreads();
       if (active) {
         for (int j = gi; j < m; j += NG) {
-          const double dx = xt - sx[j], dy = yt - sy[j], dz = zt - sz[j];
+          const double4_32a s = tile[j];
+          const double dx = xt - s.x, dy = yt - s.y, dz = zt - s.z;
           const double r2 = dx * dx + dy * dy + dz * dz;
-          const double rinv = r2 > 0.0 ? 1.0 / sqrt(r2) : 0.0;
+          const double ri = r2 > 0.0 ? 1.0 / sqrt(r2) : 0.0;
+          acc[0] += s.w * ri;
 #pragma unroll
-          for (int d = 0; d < ND; ++d) acc[d] += sw[d][j] * rinv;
+          for (int d = 1; d < ND; ++d) acc[d] += tw[d - 1][j] * ri;
         }
       }
     }
@@ -365,29 +449,16 @@ __global__ void __launch_bounds__(128) k_p2p_l2p_f64(DevGeom G, DevTaskLists L, 
   for (int d = 0; d < ND; ++d) red[d][threadIdx.x] = acc[d];
   __syncthreads();
   if (gi == 0 && active) {
-    double far[ND];
-#pragma unroll
-    for (int d = 0; d < ND; ++d) far[d] = 0.0;
-    if (loc != nullptr) {
-      const double inv_s = 1.0 / cs.w;
-      const double xs = (xt - cs.x) * inv_s, ys = (yt - cs.y) * inv_s, zs = (zt - cs.z) * inv_s;
-      double px[16], py[16], pz[16];
-      px[0] = py[0] = pz[0] = 1.0;
-      for (int k = 1; k <= G.p; ++k) { px[k] = px[k - 1] * xs; py[k] = py[k - 1] * ys; pz[k] = pz[k - 1] * zs; }
-      const double* lb = loc + (int64_t)leaf * ndp * G.np;
-      for (int q = 0; q < G.np; ++q) {
-        const int mi = G.mi[q];
-        const double mono = px[mi & 255] * py[(mi >> 8) & 255] * pz[(mi >> 16) & 255];
-#pragma unroll
-        for (int d = 0; d < ND; ++d) far[d] += lb[d * G.np + q] * mono;
-      }
-    }
+    double near[ND];
 #pragma unroll
     for (int d = 0; d < ND; ++d) {
       double s = 0.0;
       for (int g = 0; g < NG; ++g) s += red[d][g * TP + ti];
-      phi[(int64_t)d * ntp + tr.x + ti] = s * kInv4Pi + far[d];
+      near[d] = s;
     }
+    const double inv_s = 1.0 / cs.w;
+    l2p_and_store<double, ND>(G, leaf, ndp, loc, (xt - cs.x) * inv_s, (yt - cs.y) * inv_s, (zt - cs.z) * inv_s, near,
+                              tr.x + ti, ntp, phi);
   }
 }
 
@@ -414,6 +485,7 @@ cudaError_t launch_p2p_l2p_f64(const DevGeom& G, const DevTaskLists& L, const do
   P2P_DISPATCH(k_p2p_l2p_f64, G, L, W, nsrc_pts, ntgt_pts, ndp, loc, phi);
   return cudaGetLastError();
 }
+
 
 // ------------------------------------------- Galerkin sums + corrections
 // One warp per target element: u[d][e] = sum_q w_q phi[d][pos_q]

@@ -5,7 +5,7 @@
 namespace bcfmm {
 
 bool m2l_tc_supported(int) { return false; }
-cudaError_t m2l_tc_prepare_tables(int, const double*, int, M2LTensorTables*, cudaStream_t) { return cudaErrorNotSupported; }
+cudaError_t m2l_tc_prepare_tables(int, int, const double*, int, M2LTensorTables*, cudaStream_t) { return cudaErrorNotSupported; }
 cudaError_t launch_m2l_tc(const DevGeom&, const DevTaskLists&, const M2LTensorTables&, int, const float*, float*,
                           cudaStream_t) {
   return cudaErrorNotSupported;

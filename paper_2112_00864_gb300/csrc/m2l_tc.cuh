@@ -16,7 +16,7 @@ struct M2LTensorTables {
 };
 
 bool m2l_tc_supported(int p);
-cudaError_t m2l_tc_prepare_tables(int p, const double* T /*[343][np][np]*/, int nsplit, M2LTensorTables* out,
+cudaError_t m2l_tc_prepare_tables(int p, int ncode, const double* T /*[ncode][np][np]*/, int nsplit, M2LTensorTables* out,
                                   cudaStream_t st);
 cudaError_t launch_m2l_tc(const DevGeom& G, const DevTaskLists& L, const M2LTensorTables& tab, int ndp,
                           const float* mom, float* loc, cudaStream_t st);

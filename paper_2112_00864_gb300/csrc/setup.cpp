@@ -2,6 +2,7 @@
 // the adaptive octree, per-task interaction / extended-neighbour lists, the
 // near element-pair search and the translation tables.  FP64 throughout.
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -184,8 +185,23 @@ static inline uint64_t box_key(int level, int64_t i, int64_t j, int64_t k) {
   return ((uint64_t)(level + 1) << 57) | ((uint64_t)i << 38) | ((uint64_t)j << 19) | (uint64_t)k;
 }
 
-void build_lists(HostSetup& H) {
+// Same-level boxes B, C are neighbours when eta = sqrt(3)/|o| > eta0 with
+// o = ijk_B - ijk_C, i.e. |o|^2 eta0^2 < 3 (Eq. def:neighbors with the box
+// circumradius as rho).
+static std::vector<std::array<int, 3>> neighbour_offsets(double eta0) {
+  std::vector<std::array<int, 3>> out;
+  const int R = (int)std::floor(std::sqrt(3.0) / eta0) + 1;
+  for (int z = -R; z <= R; ++z)
+    for (int y = -R; y <= R; ++y)
+      for (int x = -R; x <= R; ++x)
+        if ((double)(x * x + y * y + z * z) * eta0 * eta0 < 3.0) out.push_back({x, y, z});
+  return out;
+}
+
+void build_lists(HostSetup& H, double eta0) {
   double t0 = now_s();
+  const auto NB = neighbour_offsets(eta0);
+  auto is_nb = [&](int64_t dx, int64_t dy, int64_t dz) { return (double)(dx * dx + dy * dy + dz * dz) * eta0 * eta0 < 3.0; };
   std::unordered_map<uint64_t, int> idx;
   idx.reserve(H.box.size() * 2);
   for (size_t bi = 0; bi < H.box.size(); ++bi) {
@@ -205,34 +221,45 @@ void build_lists(HostSetup& H) {
     const HostBox& B = H.box[bi];
     if (B.nchild == 0) {
       // N*: all points in neighbour subtrees at the leaf's level ...
-      for (int dz = -1; dz <= 1; ++dz) for (int dy = -1; dy <= 1; ++dy) for (int dx = -1; dx <= 1; ++dx) {
-        int c = find(B.level, B.ijk[0] + dx, B.ijk[1] + dy, B.ijk[2] + dz);
+      for (const auto& o : NB) {
+        int c = find(B.level, B.ijk[0] + o[0], B.ijk[1] + o[1], B.ijk[2] + o[2]);
         if (c >= 0) nearb[bi].push_back(c);
       }
       // ... and every coarser leaf that neighbours an ancestor
       for (int a = B.parent; a >= 0; a = H.box[a].parent) {
         const HostBox& A = H.box[a];
-        for (int dz = -1; dz <= 1; ++dz) for (int dy = -1; dy <= 1; ++dy) for (int dx = -1; dx <= 1; ++dx) {
-          int c = find(A.level, A.ijk[0] + dx, A.ijk[1] + dy, A.ijk[2] + dz);
+        for (const auto& o : NB) {
+          int c = find(A.level, A.ijk[0] + o[0], A.ijk[1] + o[1], A.ijk[2] + o[2]);
           if (c >= 0 && H.box[c].nchild == 0) nearb[bi].push_back(c);
         }
       }
     }
     if (B.level >= 2) {
       const HostBox& P = H.box[B.parent];
-      for (int dz = -1; dz <= 1; ++dz) for (int dy = -1; dy <= 1; ++dy) for (int dx = -1; dx <= 1; ++dx) {
-        int q = find(P.level, P.ijk[0] + dx, P.ijk[1] + dy, P.ijk[2] + dz);
+      for (const auto& o : NB) {
+        int q = find(P.level, P.ijk[0] + o[0], P.ijk[1] + o[1], P.ijk[2] + o[2]);
         if (q < 0) continue;
         const HostBox& Q = H.box[q];
         for (int c = Q.child0; c < Q.child0 + Q.nchild; ++c) {
           const HostBox& C = H.box[c];
-          int64_t d0 = B.ijk[0] - C.ijk[0], d1 = B.ijk[1] - C.ijk[1], d2 = B.ijk[2] - C.ijk[2];
-          if (std::llabs(d0) <= 1 && std::llabs(d1) <= 1 && std::llabs(d2) <= 1) continue;
+          if (is_nb(B.ijk[0] - C.ijk[0], B.ijk[1] - C.ijk[1], B.ijk[2] - C.ijk[2])) continue;
           vlist[bi].push_back(c);
         }
       }
     }
   }
+  // compact codes of the interaction offsets that occur
+  std::unordered_map<int64_t, int> code_of;
+  H.offsets.clear();
+  auto code = [&](int ox, int oy, int oz) -> int {
+    const int64_t key = ((int64_t)(ox + 64) << 16) | ((int64_t)(oy + 64) << 8) | (int64_t)(oz + 64);
+    auto it = code_of.find(key);
+    if (it != code_of.end()) return it->second;
+    const int c = (int)(H.offsets.size() / 3);
+    H.offsets.push_back(ox); H.offsets.push_back(oy); H.offsets.push_back(oz);
+    code_of[key] = c;
+    return c;
+  };
   static const int cls[3][2] = {{0, 0}, {0, 1}, {1, 0}};   // {source class, target class}
   for (int t = 0; t < 3; ++t) {
     HostTask& T = H.task[t];
@@ -242,6 +269,7 @@ void build_lists(HostSetup& H) {
     auto nsrc = [&](int b) { return H.box[b].pt1[sc] - H.box[b].pt0[sc]; };
     auto ntgt = [&](int b) { return H.box[b].pt1[tc] - H.box[b].pt0[tc]; };
     T.near_off.push_back(0);
+    T.run_off.push_back(0);
     T.vl_off.push_back(0);
     T.m2m_parent.assign(H.nlevels, {});
     T.l2l_child.assign(H.nlevels, {});
@@ -252,6 +280,28 @@ void build_lists(HostSetup& H) {
         for (int c : nearb[bi]) if (nsrc(c) > 0) T.near_box.push_back(c);
         T.p2p_leaf.push_back(bi);
         T.near_off.push_back((int)T.near_box.size());
+        // the same sources as merged runs of the sorted point array; for
+        // VtV the leaf's own points come first (the only run that can hold
+        // the target point itself)
+        std::vector<std::pair<int, int>> rr;
+        int self_s = -1, self_e = -1;
+        for (int c : nearb[bi]) {
+          if (nsrc(c) == 0) continue;
+          const int s0 = H.box[c].pt0[sc], s1 = H.box[c].pt1[sc];
+          if (sc == tc && c == bi) { self_s = s0; self_e = s1; continue; }
+          rr.push_back({s0, s1});
+        }
+        std::sort(rr.begin(), rr.end());
+        if (self_s >= 0) { T.runs.push_back(self_s); T.runs.push_back(self_e); }
+        T.self_len.push_back(self_s >= 0 ? self_e - self_s : 0);
+        for (size_t k = 0; k < rr.size(); ++k) {
+          if (k > 0 && T.runs.back() == rr[k].first && (int)T.runs.size() / 2 > T.run_off.back() + (self_s >= 0 ? 1 : 0)) {
+            T.runs.back() = rr[k].second;
+          } else {
+            T.runs.push_back(rr[k].first); T.runs.push_back(rr[k].second);
+          }
+        }
+        T.run_off.push_back((int)T.runs.size() / 2);
       }
       if (B.nchild == 0 && nsrc(bi) > 0) T.p2m_leaf.push_back(bi);
       if (B.nchild > 0 && nsrc(bi) > 0) T.m2m_parent[B.level].push_back(bi);
@@ -262,7 +312,7 @@ void build_lists(HostSetup& H) {
           const HostBox& C = H.box[c];
           int ox = (int)(B.ijk[0] - C.ijk[0]), oy = (int)(B.ijk[1] - C.ijk[1]), oz = (int)(B.ijk[2] - C.ijk[2]);
           T.vl_src.push_back(c);
-          T.vl_code.push_back((uint16_t)((ox + 3) + 7 * (oy + 3) + 49 * (oz + 3)));
+          T.vl_code.push_back((uint16_t)code(ox, oy, oz));
         }
         T.vl_off.push_back((int)T.vl_src.size());
         if (B.level >= 3) T.l2l_child[B.level].push_back(bi);
