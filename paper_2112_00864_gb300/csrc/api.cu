@@ -67,7 +67,7 @@ struct TaskDev {
   std::vector<int> m2m_off, l2l_off;   // host offsets into the per-level arrays
   int* m2m_parent = nullptr;
   int* l2l_child = nullptr;
-  int64_t p2p_pairs = 0, near_boxes = 0, m2l_pairs = 0, nnz = 0;
+  int64_t p2p_pairs = 0, near_boxes = 0, m2l_pairs = 0, nnz = 0, tc_entries = 0;
 };
 
 }  // namespace
@@ -89,6 +89,7 @@ struct bcfmm_ctx {
   // densities
   int ndens[2] = {0, 0}, ndp[2] = {0, 0};
   double* dens[2] = {nullptr, nullptr};
+  int* err = nullptr;                  // device error word (bounded device waits)
   // work buffers (sized for the largest ndp seen)
   int work_ndp = 0;
   double *W64 = nullptr, *mom64 = nullptr, *loc64 = nullptr, *phi = nullptr, *out_dev = nullptr;
@@ -191,6 +192,18 @@ static int upload_task(bcfmm_ctx* C, const HostSetup& H, int t) {
   int* elem_pts;
   CU(m.upload(&elem_pts, ep.data(), ep.size(), st));
   L.elem_pts = elem_pts;
+  // tensor-core M2L tiles
+  L.err = C->err;
+  L.tc_ntile = (int)T.tc_tile_off.size() > 0 ? (int)T.tc_tile_off.size() - 1 : 0;
+  if (L.tc_ntile > 0) {
+    int *tt, *to, *ec, *es;
+    CU(m.upload(&tt, T.tc_tile_tgt.data(), T.tc_tile_tgt.size(), st));
+    CU(m.upload(&to, T.tc_tile_off.data(), T.tc_tile_off.size(), st));
+    CU(m.upload(&ec, T.tc_ent_code.data(), T.tc_ent_code.size(), st));
+    CU(m.upload(&es, T.tc_ent_src.data(), T.tc_ent_src.size(), st));
+    L.tc_tile_tgt = tt; L.tc_tile_off = to; L.tc_ent_code = ec; L.tc_ent_src = es;
+    D.tc_entries = (int64_t)T.tc_ent_code.size();
+  }
   // near pairs + FP64 corrections computed on the device
   int64_t *cor_off;
   int *cor_col, *cor_row;
@@ -260,8 +273,11 @@ static int build_impl(const double* verts, int64_t nvert, const int32_t* tets, i
     return fail(BCFMM_ERR_ARG, "build_bc_tree: near_n must be in 1..8 and near_k in 0..3");
   if (prm.precision < BCFMM_FP64 || prm.precision > BCFMM_FP32_BF16X3)
     return fail(BCFMM_ERR_ARG, "build_bc_tree: unknown precision");
-  if ((prm.precision == BCFMM_FP32_BF16X2 || prm.precision == BCFMM_FP32_BF16X3) && !m2l_tc_supported(prm.p))
-    return fail(BCFMM_ERR_ARG, "build_bc_tree: the tensor-core M2L supports p <= " + std::to_string(kTcMaxP));
+  const bool tc_mode = prm.precision == BCFMM_FP32_BF16X2 || prm.precision == BCFMM_FP32_BF16X3;
+  const int nsplit = prm.precision == BCFMM_FP32_BF16X3 ? 3 : 2;
+  if (tc_mode && !m2l_tc_supported(prm.p, nsplit))
+    return fail(BCFMM_ERR_ARG, "build_bc_tree: the tensor-core M2L supports p <= " + std::to_string(kTcMaxP) +
+                                   (nsplit == 3 ? " (p <= 6 with the 3-term split)" : ""));
 
   HostSetup H;
   bool mesh_err = false;
@@ -284,6 +300,10 @@ static int build_impl(const double* verts, int64_t nvert, const int32_t* tets, i
       return cleanup(fail(BCFMM_ERR_MESH, "build_bc_tree: more than 128 coincident points in one leaf at the deepest level"));
   build_lists(H, prm.eta0);
   if (H.offsets.size() / 3 > 65535) return cleanup(fail(BCFMM_ERR_ARG, "build_bc_tree: too many interaction offsets"));
+  if (tc_mode)
+    for (int t = 0; t < 3; ++t) build_tc_tiles(H, t, 128);
+  if (C->mem.alloc(&C->err, 1) != cudaSuccess || cudaMemsetAsync(C->err, 0, sizeof(int), C->st) != cudaSuccess)
+    return cleanup(fail(BCFMM_ERR_OOM, "build_bc_tree: device allocation failed (error word)"));
   find_near_pairs(H, prm.eta_ns);
   C->sec_tree = H.seconds_tree;
   C->sec_lists = H.seconds_lists;
@@ -298,7 +318,7 @@ static int build_impl(const double* verts, int64_t nvert, const int32_t* tets, i
   cudaStream_t st = C->st;
   auto& m = C->mem;
   DevGeom& G = C->G;
-  G.np = C->np; G.p = prm.p; G.nbox = C->nbox;
+  G.np = C->np; G.ms = (C->np + 3) / 4 * 4; G.p = prm.p; G.nbox = C->nbox;
   {
     MultiIndex M; M.init(prm.p);
     std::vector<int> mi(M.n), tk(M.n);
@@ -390,7 +410,7 @@ static int build_impl(const double* verts, int64_t nvert, const int32_t* tets, i
               m.upload(&C->L2L32, L32.data(), L32.size(), st) == cudaSuccess;
     if (!ok) return cleanup(fail(BCFMM_ERR_OOM, "build_bc_tree: device allocation failed (tables)"));
     if (prm.precision == BCFMM_FP32_BF16X2 || prm.precision == BCFMM_FP32_BF16X3) {
-      cudaError_t ce = m2l_tc_prepare_tables(prm.p, ncode, T.data(), prm.precision == BCFMM_FP32_BF16X3 ? 3 : 2, &C->tc, st);
+      cudaError_t ce = m2l_tc_prepare_tables(prm.p, ncode, T.data(), nsplit, &C->tc, st);
       if (ce != cudaSuccess) return cleanup(fail(BCFMM_ERR_CUDA, std::string("build_bc_tree: tensor tables: ") + cudaGetErrorString(ce)));
     }
   }
@@ -432,7 +452,7 @@ static int ensure_work(bcfmm_ctx* C, int ndp) {
     if (p) m.release(p);
   const int64_t npmax = std::max(C->npts[0], C->npts[1]);
   const int64_t nel = std::max(C->ntet, C->ntri);
-  const size_t nexp = (size_t)C->nbox * ndp * C->np;
+  const size_t nexp = (size_t)C->nbox * ndp * C->G.ms;
   const bool f64 = C->prm.precision == BCFMM_FP64;
   CU(m.alloc(&C->phi, (size_t)ndp * npmax));
   CU(m.alloc(&C->out_dev, (size_t)ndp * nel));
@@ -489,7 +509,7 @@ static int eval_impl(bcfmm_ctx* C, int t, double* out, int out_is_device) {
   const DevGeom& G = C->G;
   const int64_t nsp = C->npts[L.src_cls], ntp = C->npts[L.tgt_cls];
   const int64_t nsel = kind == 0 ? C->ntet : C->ntri;
-  const size_t nexp = (size_t)C->nbox * ndp * C->np;
+  const size_t nexp = (size_t)C->nbox * ndp * C->G.ms;
   const bool f64 = C->prm.precision == BCFMM_FP64;
   const bool tc = C->prm.precision == BCFMM_FP32_BF16X2 || C->prm.precision == BCFMM_FP32_BF16X3;
   const bool tm = C->prm.timing && C->ev_ok;
@@ -541,7 +561,13 @@ static int eval_impl(bcfmm_ctx* C, int t, double* out, int out_is_device) {
   if (tm) CU(cudaEventRecord(ev[6], st));
   if (!out_is_device) {
     CU(cudaMemcpyAsync(out, C->out_dev, (size_t)ndens * L.ntgt_el * sizeof(double), cudaMemcpyDeviceToHost, st));
+    int herr = 0;
+    CU(cudaMemcpyAsync(&herr, C->err, sizeof(int), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
+    if (herr) {
+      CU(cudaMemsetAsync(C->err, 0, sizeof(int), st));
+      return fail(BCFMM_ERR_TIMEOUT, "eval: a bounded device wait expired (tensor-core M2L); results are invalid");
+    }
   }
   C->ev_rec[t] = tm;
   return BCFMM_OK;
@@ -561,6 +587,11 @@ extern "C" int bcfmm_stats(const bcfmm_ctx* C, char* json, size_t cap) {
   };
   kv("ntet", (double)C->ntet); kv("ntri", (double)C->ntri);
   kv("npts_tet", (double)C->npts[0]); kv("npts_tri", (double)C->npts[1]);
+  {
+    int herr = 0;
+    if (C->err) { cudaMemcpy(&herr, C->err, sizeof(int), cudaMemcpyDeviceToHost); }
+    kv("device_error", herr);
+  }
   kv("p", C->prm.p); kv("np", C->np); kv("eta0", C->prm.eta0); kv("n_offsets", C->ncode); kv("leaf_size", C->prm.leaf_size); kv("precision", C->prm.precision);
   kv("nbox", C->nbox); kv("nleaf", C->nleaf); kv("nlevels", C->nlevels);
   kv("setup_s", C->sec_setup); kv("tree_s", C->sec_tree); kv("lists_s", C->sec_lists);
@@ -570,10 +601,10 @@ extern "C" int bcfmm_stats(const bcfmm_ctx* C, char* json, size_t cap) {
     char b[400];
     snprintf(b, sizeof b,
              "\"%s\": {\"p2p_pairs\": %lld, \"near_boxes\": %lld, \"m2l_pairs\": %lld, \"near_pairs\": %lld, "
-             "\"p2p_leaves\": %d, \"m2l_targets\": %d, \"p2m_leaves\": %d}, ",
+             "\"p2p_leaves\": %d, \"m2l_targets\": %d, \"p2m_leaves\": %d, \"tc_entries\": %lld}, ",
              names[t], (long long)C->task[t].p2p_pairs, (long long)C->task[t].near_boxes,
              (long long)C->task[t].m2l_pairs, (long long)C->task[t].nnz, C->task[t].L.n_p2p, C->task[t].L.n_m2l,
-             C->task[t].L.n_p2m);
+             C->task[t].L.n_p2m, (long long)C->task[t].tc_entries);
     s += b;
   }
   // stages: weights+clear, P2M+M2M, M2L, L2L, L2P+P2P, element sums+corrections

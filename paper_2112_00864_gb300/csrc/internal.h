@@ -49,6 +49,8 @@ struct HostTask {
   std::vector<std::vector<int>> m2m_parent;        // per level: non-leaf boxes with source points
   std::vector<std::vector<int>> l2l_child;         // per level: boxes (level>=3) with target points
   std::vector<int> l2p_leaf;                       // leaves (level >= 2) with target points
+  // tensor-core M2L tiles (see DevTaskLists)
+  std::vector<int> tc_tile_tgt, tc_tile_off, tc_ent_code, tc_ent_src;
   // near element pairs, CSR over target elements
   std::vector<int64_t> cor_off;
   std::vector<int32_t> cor_col;
@@ -79,6 +81,7 @@ std::string setup_mesh(HostSetup& H, const double* verts, int64_t nvert, const i
                        int64_t ntet, const int32_t* tris, int64_t ntri, bool* mesh_err);
 void build_tree(HostSetup& H, int leaf_size);
 void build_lists(HostSetup& H, double eta0);
+void build_tc_tiles(HostSetup& H, int task, int tile_m);
 void find_near_pairs(HostSetup& H, double eta_ns);
 
 // Gauss-Legendre nodes/weights on [0,1] (Newton iteration on P_n).

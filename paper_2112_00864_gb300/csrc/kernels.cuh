@@ -8,6 +8,7 @@ namespace bcfmm {
 // Geometry and lists the evaluation kernels read (device pointers).
 struct DevGeom {
   int np;                        // nterms(p)
+  int ms;                        // row stride of moment / local arrays (np rounded up to 4)
   int p;
   int nbox;
   const int* mi;                 // packed multi-indices a | b << 8 | c << 16, degree-major
@@ -35,6 +36,14 @@ struct DevTaskLists {
   const int* elem_pts;           // [ntgt_el][4] sorted positions of the element's points (-1 pad)
   int nq_tgt;                    // 4 (tets) or 3 (triangles)
   int src_cls, tgt_cls;
+  // tensor-core M2L tiles: 128 same-level, same-octant targets per tile and,
+  // per (tile, offset) entry, the source box of every row (-1: none)
+  int tc_ntile;
+  const int* tc_tile_tgt;        // [ntile][128]
+  const int* tc_tile_off;        // [ntile+1]
+  const int* tc_ent_code;        // [nent]
+  const int* tc_ent_src;         // [nent][128]
+  int* err;                      // device error word (bounded waits)
 };
 
 // launchers (return cudaGetLastError())

@@ -71,7 +71,7 @@ __global__ void k_p2m(DevGeom G, const int* __restrict__ leaves, int cls, const 
       for (int dd = 0; dd < ndp; ++dd) {
         T acc = 0;
         for (int j = 0; j < m; ++j) acc += ws[dd * 64 + j] * px[j] * py[j] * pz[j];
-        mom[((int64_t)leaf * ndp + dd) * np + q] += acc;
+        mom[((int64_t)leaf * ndp + dd) * G.ms + q] += acc;
       }
     }
   }
@@ -101,7 +101,7 @@ __global__ void k_m2m(DevGeom G, const int* __restrict__ parents, const T* __res
     __syncthreads();
     for (int i = threadIdx.x; i < nc * np; i += blockDim.x) {
       int c = i / np, q = i % np;
-      mc[i] = mom[((int64_t)(c0 + c) * ndp + d) * np + q];
+      mc[i] = mom[((int64_t)(c0 + c) * ndp + d) * G.ms + q];
     }
     __syncthreads();
     for (int b = threadIdx.x; b < np; b += blockDim.x) {
@@ -110,7 +110,7 @@ __global__ void k_m2m(DevGeom G, const int* __restrict__ parents, const T* __res
         const T* Mt = M2M + (int64_t)G.box_octant[c0 + c] * np * np;
         for (int g = 0; g <= b; ++g) acc += Mt[(int64_t)g * np + b] * mc[c * np + g];   // g <= b
       }
-      mom[((int64_t)P * ndp + d) * np + b] = acc;
+      mom[((int64_t)P * ndp + d) * G.ms + b] = acc;
     }
   }
 }
@@ -145,7 +145,7 @@ __global__ void k_m2l_simt(DevGeom G, DevTaskLists L, const T* __restrict__ Tt, 
     const int sb = L.vl_src[e];
     const T* Tc = Tt + (int64_t)L.vl_code[e] * np * np;
     __syncthreads();
-    for (int i = threadIdx.x; i < ND * np; i += blockDim.x) ms[i] = mom[(int64_t)sb * ndp * np + i];
+    for (int i = threadIdx.x; i < ND * np; i += blockDim.x) ms[i] = mom[((int64_t)sb * ndp + i / np) * G.ms + i % np];
     __syncthreads();
     if (a < np) {
       T part[ND];
@@ -163,7 +163,7 @@ __global__ void k_m2l_simt(DevGeom G, DevTaskLists L, const T* __restrict__ Tt, 
   if (a < np) {
     const double inv_s = 1.0 / G.box_cs[tb].w;
 #pragma unroll
-    for (int d = 0; d < ND; ++d) loc[((int64_t)tb * ndp + d) * np + a] = (T)(acc[d] * inv_s);
+    for (int d = 0; d < ND; ++d) loc[((int64_t)tb * ndp + d) * G.ms + a] = (T)(acc[d] * inv_s);
   }
 }
 
@@ -198,12 +198,12 @@ __global__ void k_l2l(DevGeom G, const int* __restrict__ children, const T* __re
   const T* Lm = L2L + (int64_t)G.box_octant[C] * np * np;
   for (int d = 0; d < ndp; ++d) {
     __syncthreads();
-    for (int i = threadIdx.x; i < np; i += blockDim.x) lp[i] = loc[((int64_t)P * ndp + d) * np + i];
+    for (int i = threadIdx.x; i < np; i += blockDim.x) lp[i] = loc[((int64_t)P * ndp + d) * G.ms + i];
     __syncthreads();
     for (int a = threadIdx.x; a < np; a += blockDim.x) {
       T acc = 0;
       for (int b = a; b < np; ++b) acc += Lm[(int64_t)b * np + a] * lp[b];
-      loc[((int64_t)C * ndp + d) * np + a] += acc;
+      loc[((int64_t)C * ndp + d) * G.ms + a] += acc;
     }
   }
 }
@@ -275,12 +275,12 @@ __device__ __forceinline__ void l2p_and_store(const DevGeom& G, int leaf, int nd
     T px[16], py[16], pz[16];
     px[0] = py[0] = pz[0] = (T)1;
     for (int k = 1; k <= G.p; ++k) { px[k] = px[k - 1] * (T)xs; py[k] = py[k - 1] * (T)ys; pz[k] = pz[k - 1] * (T)zs; }
-    const T* lb = loc + (int64_t)leaf * ndp * G.np;
+    const T* lb = loc + (int64_t)leaf * ndp * G.ms;
     for (int q = 0; q < G.np; ++q) {
       const int mi = G.mi[q];
       const T mono = px[mi & 255] * py[(mi >> 8) & 255] * pz[(mi >> 16) & 255];
 #pragma unroll
-      for (int d = 0; d < ND; ++d) far[d] += (double)(lb[d * G.np + q] * mono);
+      for (int d = 0; d < ND; ++d) far[d] += (double)(lb[d * G.ms + q] * mono);
     }
   }
 #pragma unroll

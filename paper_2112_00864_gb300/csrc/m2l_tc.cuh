@@ -6,7 +6,7 @@
 
 namespace bcfmm {
 
-constexpr int kTcMaxP = 8;
+constexpr int kTcMaxP = 7;
 
 // Device tables of the tensor-core M2L (BF16 split parts of the box-scaled
 // translation matrices, one per offset code).
@@ -15,7 +15,8 @@ struct M2LTensorTables {
   int p = 0, nsplit = 0;
 };
 
-bool m2l_tc_supported(int p);
+bool m2l_tc_supported(int p, int nsplit);
+int m2l_tc_smem_bytes(int p, int nsplit);
 cudaError_t m2l_tc_prepare_tables(int p, int ncode, const double* T /*[ncode][np][np]*/, int nsplit, M2LTensorTables* out,
                                   cudaStream_t st);
 cudaError_t launch_m2l_tc(const DevGeom& G, const DevTaskLists& L, const M2LTensorTables& tab, int ndp,

@@ -323,6 +323,60 @@ void build_lists(HostSetup& H, double eta0) {
   H.seconds_lists = now_s() - t0;
 }
 
+// Tiles of the tensor-core interaction phase: M2L targets grouped by
+// (level, octant in the parent), tile_m per tile; per tile the offsets that
+// occur, each with the source box of every row.
+void build_tc_tiles(HostSetup& H, int t, int tile_m) {
+  HostTask& T = H.task[t];
+  const int n = (int)T.m2l_tgt.size();
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    const HostBox& A = H.box[T.m2l_tgt[x]];
+    const HostBox& B = H.box[T.m2l_tgt[y]];
+    return A.level != B.level ? A.level < B.level : A.octant < B.octant;
+  });
+  T.tc_tile_tgt.clear(); T.tc_tile_off.assign(1, 0); T.tc_ent_code.clear(); T.tc_ent_src.clear();
+  int i = 0;
+  while (i < n) {
+    const HostBox& F = H.box[T.m2l_tgt[order[i]]];
+    int j = i;
+    std::vector<int> rows;
+    while (j < n && (int)rows.size() < tile_m) {
+      const HostBox& B = H.box[T.m2l_tgt[order[j]]];
+      if (B.level != F.level || B.octant != F.octant) break;
+      rows.push_back(order[j]);
+      ++j;
+    }
+    std::unordered_map<int, int> ent_of;
+    std::vector<std::pair<int, std::vector<int>>> ents;
+    for (int r = 0; r < (int)rows.size(); ++r) {
+      const int k = rows[r];
+      for (int e = T.vl_off[k]; e < T.vl_off[k + 1]; ++e) {
+        const int code = T.vl_code[e];
+        auto it = ent_of.find(code);
+        int idx;
+        if (it == ent_of.end()) {
+          idx = (int)ents.size();
+          ent_of[code] = idx;
+          ents.push_back({code, std::vector<int>(tile_m, -1)});
+        } else {
+          idx = it->second;
+        }
+        ents[idx].second[r] = T.vl_src[e];
+      }
+    }
+    std::sort(ents.begin(), ents.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+    for (int r = 0; r < tile_m; ++r) T.tc_tile_tgt.push_back(r < (int)rows.size() ? T.m2l_tgt[rows[r]] : -1);
+    for (auto& en : ents) {
+      T.tc_ent_code.push_back(en.first);
+      T.tc_ent_src.insert(T.tc_ent_src.end(), en.second.begin(), en.second.end());
+    }
+    T.tc_tile_off.push_back((int)T.tc_ent_code.size());
+    i = j;
+  }
+}
+
 // ------------------------------------------------------------ near pairs
 // near iff eta = (rho_t + rho_s)/|x_t - x_s| > eta_ns (eta = inf for equal
 // centres), x = centroid, rho = largest vertex distance from the centroid.

@@ -70,6 +70,25 @@ def test_fp32_matches_oracle(bc, c1, task):
     assert r2 <= 1e-6, (r2, rm)
 
 
+@pytest.mark.parametrize("prec", ["bf16x2", "bf16x3"])
+@pytest.mark.parametrize("task", ["vtv", "btv"])
+def test_tensor_core_m2l_matches_oracle(bc, c1, prec, task):
+    """tcgen05 M2L (BF16 split, FP32 accumulation, compensated window sums)
+    against O2 at the same p (precision error only) and O1."""
+    m, f, g = c1
+    dens = g if task == "btv" else f
+    kind = bc.BOUNDARY if task == "btv" else bc.VOLUME
+    ctx = bc.Context.from_mesh(m, p=6, leaf_size=64, precision=prec)
+    ctx.set_density(kind, dens)
+    u = ctx.eval(task).cpu().numpy()
+    assert ctx.stats()["device_error"] == 0
+    ref = O.fmm(task, m, dens, p=6, leaf_size=64)
+    r2, rm = rel(u, ref, _sizes(m, task))
+    assert r2 <= 1e-6, (r2, rm)
+    r2, rm = rel(u, O.direct(task, m, dens), _sizes(m, task))
+    assert r2 <= 1.5e-6, (r2, rm)
+
+
 def test_multiple_densities_and_device_io(bc, c1):
     m, f, g = c1
     rng = np.random.default_rng(7)
@@ -126,12 +145,12 @@ def test_degenerate_meshes(bc):
 
 
 def test_ball_full_size_sampled(bc):
-    """Config-2 workload (unit ball, 5120 boundary triangles, ~1.9e5 tets):
-    FP32 path at the benchmark's p = 6, eta0 = 0.5 against O1 on sampled
-    target elements."""
+    """Config-2 workload (unit ball, 5120 boundary triangles, ~1.9e5 tets)
+    in the benchmark's launch configuration (p = 6, eta0 = 0.5, leaf 128,
+    BF16x2 tensor-core M2L) against O1 on sampled target elements."""
     m = ball_bc_mesh(4, radial=0.35)
     f = np.ones((1, m.ntet))
-    ctx = bc.Context.from_mesh(m, p=6, eta0=0.5, leaf_size=64, precision="fp32")
+    ctx = bc.Context.from_mesh(m, p=6, eta0=0.5, leaf_size=128, precision="bf16x2")
     ctx.set_density(bc.VOLUME, f)
     rng = np.random.default_rng(11)
     for task, nel, size in (("vtv", m.ntet, O.element_volumes(m)), ("vtb", m.ntri, O.element_areas(m))):
