@@ -90,6 +90,9 @@ struct bcfmm_ctx {
   int ndens[2] = {0, 0}, ndp[2] = {0, 0};
   double* dens[2] = {nullptr, nullptr};
   int* err = nullptr;                  // device error word (bounded device waits)
+  int tc_max_units = 0;                // largest tensor-core work-unit count over the tasks
+  float2* tc_partial = nullptr;        // unit partial sums of the tensor-core M2L
+  uint8_t* tc_momb = nullptr;          // BF16 split moments of the tensor-core M2L
   // work buffers (sized for the largest ndp seen)
   int work_ndp = 0;
   double *W64 = nullptr, *mom64 = nullptr, *loc64 = nullptr, *phi = nullptr, *out_dev = nullptr;
@@ -203,6 +206,29 @@ static int upload_task(bcfmm_ctx* C, const HostSetup& H, int t) {
     CU(m.upload(&es, T.tc_ent_src.data(), T.tc_ent_src.size(), st));
     L.tc_tile_tgt = tt; L.tc_tile_off = to; L.tc_ent_code = ec; L.tc_ent_src = es;
     D.tc_entries = (int64_t)T.tc_ent_code.size();
+    // work units: each tile's offsets cut into runs of U entries, U chosen
+    // so that there are about 4 units per SM (load balance); a tile without
+    // offsets still gets one (empty) unit that writes zeros
+    int nsm = 152;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, C->device);
+    const int64_t E = D.tc_entries;
+    const int U = (int)std::max<int64_t>(8, (E + 4 * nsm - 1) / (4 * nsm));
+    std::vector<int4> units;
+    std::vector<int> tile_unit_off(1, 0);
+    for (int tl = 0; tl < L.tc_ntile; ++tl) {
+      const int a = T.tc_tile_off[tl], b = T.tc_tile_off[tl + 1];
+      if (a == b) units.push_back(make_int4(tl, a, b, 0));
+      for (int x = a; x < b; x += U) units.push_back(make_int4(tl, x, std::min(b, x + U), 0));
+      tile_unit_off.push_back((int)units.size());
+    }
+    int4* du;
+    int* dto;
+    CU(m.upload(&du, units.data(), units.size(), st));
+    CU(m.upload(&dto, tile_unit_off.data(), tile_unit_off.size(), st));
+    L.tc_units = du;
+    L.tc_tile_unit_off = dto;
+    L.tc_nunit = (int)units.size();
+    C->tc_max_units = std::max(C->tc_max_units, L.tc_nunit);
   }
   // near pairs + FP64 corrections computed on the device
   int64_t *cor_off;
@@ -448,8 +474,10 @@ static int ensure_work(bcfmm_ctx* C, int ndp) {
   if (C->work_ndp >= ndp) return BCFMM_OK;
   auto& m = C->mem;
   for (void* p : {(void*)C->W64, (void*)C->mom64, (void*)C->loc64, (void*)C->phi, (void*)C->out_dev, (void*)C->W32,
-                  (void*)C->mom32, (void*)C->loc32})
+                  (void*)C->mom32, (void*)C->loc32, (void*)C->tc_partial, (void*)C->tc_momb})
     if (p) m.release(p);
+  C->tc_partial = nullptr;
+  C->tc_momb = nullptr;
   const int64_t npmax = std::max(C->npts[0], C->npts[1]);
   const int64_t nel = std::max(C->ntet, C->ntri);
   const size_t nexp = (size_t)C->nbox * ndp * C->G.ms;
@@ -466,6 +494,10 @@ static int ensure_work(bcfmm_ctx* C, int ndp) {
     CU(m.alloc(&C->mom32, nexp));
     CU(m.alloc(&C->loc32, nexp));
     C->W64 = C->mom64 = C->loc64 = nullptr;
+    if (C->tc.tab != nullptr && C->tc_max_units > 0) {
+      CU(m.alloc(&C->tc_partial, (size_t)ndp * C->tc_max_units * C->tc.npad * 128));
+      CU(m.alloc(&C->tc_momb, (size_t)C->nbox * ndp * C->tc.nsplit * C->tc.kpad * 2));
+    }
   }
   C->work_ndp = ndp;
   return BCFMM_OK;
@@ -546,7 +578,7 @@ static int eval_impl(bcfmm_ctx* C, int t, double* out, int out_is_device) {
       CU(launch_m2m<float>(G, D.m2m_parent + D.m2m_off[l], n, C->M2M32, ndp, C->mom32, st));
     }
     if (tm) CU(cudaEventRecord(ev[2], st));
-    if (tc) CU(launch_m2l_tc(G, L, C->tc, ndp, C->mom32, C->loc32, st));
+    if (tc) CU(launch_m2l_tc(G, L, C->tc, ndp, C->mom32, C->loc32, C->tc_partial, C->tc_momb, st));
     else CU(launch_m2l_simt<float>(G, L, C->T32, G.tri_k, ndp, C->mom32, C->loc32, st));
     if (tm) CU(cudaEventRecord(ev[3], st));
     for (int l = 3; l < C->nlevels; ++l) {

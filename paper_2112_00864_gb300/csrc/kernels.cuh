@@ -43,6 +43,9 @@ struct DevTaskLists {
   const int* tc_tile_off;        // [ntile+1]
   const int* tc_ent_code;        // [nent]
   const int* tc_ent_src;         // [nent][128]
+  int tc_nunit;                  // work units: (tile, entry range)
+  const int4* tc_units;          // [nunit]
+  const int* tc_tile_unit_off;   // [ntile+1] units of each tile, in order
   int* err;                      // device error word (bounded waits)
 };
 

@@ -12,15 +12,19 @@ constexpr int kTcMaxP = 7;
 // translation matrices, one per offset code).
 struct M2LTensorTables {
   void* tab = nullptr;   // bf16 parts, layout private to m2l_tc.cu
-  int p = 0, nsplit = 0;
+  int p = 0, nsplit = 0, npad = 0, kpad = 0;
 };
 
 bool m2l_tc_supported(int p, int nsplit);
 int m2l_tc_smem_bytes(int p, int nsplit);
 cudaError_t m2l_tc_prepare_tables(int p, int ncode, const double* T /*[ncode][np][np]*/, int nsplit, M2LTensorTables* out,
                                   cudaStream_t st);
+// Scratch (device memory owned by the caller):
+//   partial: ndp * L.tc_nunit * npad * 128 float2 (unit partial sums)
+//   momb:    nbox * ndp * nsplit * kpad BF16 (split moments)
 cudaError_t launch_m2l_tc(const DevGeom& G, const DevTaskLists& L, const M2LTensorTables& tab, int ndp,
-                          const float* mom, float* loc, cudaStream_t st);
+                          const float* mom, float* loc, float2* partial, void* momb, cudaStream_t st);
+int m2l_tc_npad(int p);
 void m2l_tc_free_tables(M2LTensorTables* t);
 
 }  // namespace bcfmm
