@@ -266,9 +266,9 @@ template <typename T, int ND>
 __device__ __forceinline__ void l2p_and_store(const DevGeom& G, int leaf, int ndp, const T* __restrict__ loc,
                                               double xs, double ys, double zs, const double* near, int64_t pos,
                                               int64_t ntp, double* __restrict__ phi) {
-  double far[ND];
+  T far[ND];
 #pragma unroll
-  for (int d = 0; d < ND; ++d) far[d] = 0.0;
+  for (int d = 0; d < ND; ++d) far[d] = (T)0;
   // L2P: phi_far(x) = sum_a l^a xhat^a, xhat = (x - c)/s (locals of boxes
   // without an interaction list are zero)
   if (loc != nullptr) {
@@ -280,21 +280,33 @@ __device__ __forceinline__ void l2p_and_store(const DevGeom& G, int leaf, int nd
       const int mi = G.mi[q];
       const T mono = px[mi & 255] * py[(mi >> 8) & 255] * pz[(mi >> 16) & 255];
 #pragma unroll
-      for (int d = 0; d < ND; ++d) far[d] += (double)(lb[d * G.ms + q] * mono);
+      for (int d = 0; d < ND; ++d) far[d] += lb[d * G.ms + q] * mono;
     }
   }
 #pragma unroll
-  for (int d = 0; d < ND; ++d) phi[(int64_t)d * ntp + pos] = near[d] * kInv4Pi + far[d];
+  for (int d = 0; d < ND; ++d) phi[(int64_t)d * ntp + pos] = near[d] * kInv4Pi + (double)far[d];
 }
 
+__device__ __forceinline__ void two_sum_f(float& hi, float& lo, float x) {
+  const float s = hi + x;
+  const float bb = s - hi;
+  lo += (hi - (s - bb)) + (x - bb);
+  hi = s;
+}
+
+// Two targets per thread (ND <= 2) or one (ND > 2); thread groups split the
+// source tile; source tiles are double-buffered (one barrier per tile); the
+// per-tile FP32 sums are folded with a compensated (hi + lo) FP32 sum.
 template <int ND>
 __global__ void __launch_bounds__(128) k_p2p_l2p_f32(DevGeom G, DevTaskLists L, const float* __restrict__ W,
                                                      int64_t nsp, int64_t ntp, int ndp,
                                                      const float* __restrict__ loc, double* __restrict__ phi) {
-  __shared__ float4 tile[kTile];
-  __shared__ float tw[ND > 1 ? ND - 1 : 1][kTile];
+  constexpr int TPT = ND <= 2 ? 2 : 1;
+  constexpr int PPT = kTile / 128;                 // source points loaded per thread per tile
+  __shared__ float4 tile[2][kTile];
+  __shared__ float tw[2][ND > 1 ? ND - 1 : 1][kTile];
   __shared__ int pre[kRunBatch + 1], rst[kRunBatch];
-  __shared__ double red[ND][128];
+  __shared__ float2 red[ND][128 * TPT];
   const int b = blockIdx.x;
   const int leaf = L.p2p_leaf[b];
   const int sc = L.src_cls, tc = L.tgt_cls;
@@ -303,87 +315,141 @@ __global__ void __launch_bounds__(128) k_p2p_l2p_f32(DevGeom G, DevTaskLists L, 
   split_df(cs.x, chx, clx); split_df(cs.y, chy, cly); split_df(cs.z, chz, clz);
   const int2 tr = G.box_rng[tc][leaf];
   const int nt = tr.y - tr.x;
-  const int TP = nt <= 8 ? 8 : (nt <= 16 ? 16 : (nt <= 32 ? 32 : (nt <= 64 ? 64 : 128)));
-  const int NG = 128 / TP;
-  const int ti = threadIdx.x % TP, gi = threadIdx.x / TP;
-  const bool active = ti < nt;
-  float xt = 0.f, yt = 0.f, zt = 0.f;
-  if (active) {
-    const float4 h = G.pthi[tc][tr.x + ti], l = G.ptlo[tc][tr.x + ti];
-    xt = (h.x - chx) + (l.x - clx);
-    yt = (h.y - chy) + (l.y - cly);
-    zt = (h.z - chz) + (l.z - clz);
-  }
-  double accd[ND];
+  const int slots = (nt + TPT - 1) / TPT;
+  const int TS = slots <= 8 ? 8 : (slots <= 16 ? 16 : (slots <= 32 ? 32 : (slots <= 64 ? 64 : 128)));
+  const int NG = 128 / TS;
+  const int ts = threadIdx.x % TS, gi = threadIdx.x / TS;
+  float xt[TPT], yt[TPT], zt[TPT];
+  bool act[TPT];
 #pragma unroll
-  for (int d = 0; d < ND; ++d) accd[d] = 0.0;
+  for (int u = 0; u < TPT; ++u) {
+    const int t = ts + u * TS;
+    act[u] = t < nt;
+    xt[u] = yt[u] = zt[u] = 1e30f;      // padding targets: far away, discarded
+    if (act[u]) {
+      const float4 h = G.pthi[tc][tr.x + t], l = G.ptlo[tc][tr.x + t];
+      xt[u] = (h.x - chx) + (l.x - clx);
+      yt[u] = (h.y - chy) + (l.y - cly);
+      zt[u] = (h.z - chz) + (l.z - clz);
+    }
+  }
+  float shi[TPT][ND], slo[TPT][ND];
+#pragma unroll
+  for (int u = 0; u < TPT; ++u)
+#pragma unroll
+    for (int d = 0; d < ND; ++d) shi[u][d] = slo[u][d] = 0.f;
   const int r0 = L.run_off[b], r1 = L.run_off[b + 1];
   const int self_len = L.self_len[b];
+  float4 reg[PPT];
+  float regw[PPT][ND > 1 ? ND - 1 : 1];
   for (int rb = r0; rb < r1; rb += kRunBatch) {
     const int nr = min(kRunBatch, r1 - rb);
     __syncthreads();
     scan_runs(L.runs + rb, nr, pre, rst);
     __syncthreads();
     const int total = pre[nr];
-    for (int j0 = 0; j0 < total; j0 += kTile) {
-      const int m = min(kTile, total - j0);
-      __syncthreads();
-      for (int j = threadIdx.x; j < m; j += 128) {
-        const int v = j0 + j;
-        const int r = find_run(pre, nr, v);
-        const int src = rst[r] + (v - pre[r]);
-        const float4 h = G.pthi[sc][src], l = G.ptlo[sc][src];
-        tile[j] = make_float4((h.x - chx) + (l.x - clx), (h.y - chy) + (l.y - cly), (h.z - chz) + (l.z - clz), W[src]);
+    const int ntiles = (total + kTile - 1) / kTile;
+    auto load_tile = [&](int t) {
 #pragma unroll
-        for (int d = 1; d < ND; ++d) tw[d - 1][j] = W[(int64_t)d * nsp + src];
+      for (int q = 0; q < PPT; ++q) {
+        const int v = t * kTile + threadIdx.x + q * 128;
+        if (v < total) {
+          const int r = find_run(pre, nr, v);
+          const int src = rst[r] + (v - pre[r]);
+          const float4 h = G.pthi[sc][src], l = G.ptlo[sc][src];
+          reg[q] = make_float4((h.x - chx) + (l.x - clx), (h.y - chy) + (l.y - cly), (h.z - chz) + (l.z - clz), W[src]);
+#pragma unroll
+          for (int d = 1; d < ND; ++d) regw[q][d - 1] = W[(int64_t)d * nsp + src];
+        }
       }
-      __syncthreads();
-      if (active) {
-        float acc[ND];
+    };
+    auto store_tile = [&](int buf) {
 #pragma unroll
-        for (int d = 0; d < ND; ++d) acc[d] = 0.f;
-        if (rb == r0 && j0 < self_len) {
-          for (int j = gi; j < m; j += NG) {
-            const float4 s = tile[j];
-            const float dx = xt - s.x, dy = yt - s.y, dz = zt - s.z;
+      for (int q = 0; q < PPT; ++q) {
+        const int j = threadIdx.x + q * 128;
+        tile[buf][j] = reg[q];
+#pragma unroll
+        for (int d = 1; d < ND; ++d) tw[buf][d - 1][j] = regw[q][d - 1];
+      }
+    };
+    if (ntiles > 0) {
+      load_tile(0);
+      store_tile(0);
+    }
+    __syncthreads();
+    for (int t = 0; t < ntiles; ++t) {
+      const int cur = t & 1;
+      if (t + 1 < ntiles) load_tile(t + 1);      // global loads in flight during the compute
+      const int m = min(kTile, total - t * kTile);
+      float acc[TPT][ND];
+#pragma unroll
+      for (int u = 0; u < TPT; ++u)
+#pragma unroll
+        for (int d = 0; d < ND; ++d) acc[u][d] = 0.f;
+      if (rb == r0 && t * kTile < self_len) {
+        for (int j = gi; j < m; j += NG) {
+          const float4 s = tile[cur][j];
+#pragma unroll
+          for (int u = 0; u < TPT; ++u) {
+            const float dx = xt[u] - s.x, dy = yt[u] - s.y, dz = zt[u] - s.z;
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
             const float ri = r2 > 0.f ? rsqrtf(r2) : 0.f;
-            acc[0] = fmaf(s.w, ri, acc[0]);
+            acc[u][0] = fmaf(s.w, ri, acc[u][0]);
 #pragma unroll
-            for (int d = 1; d < ND; ++d) acc[d] = fmaf(tw[d - 1][j], ri, acc[d]);
-          }
-        } else {
-#pragma unroll 4
-          for (int j = gi; j < m; j += NG) {
-            const float4 s = tile[j];
-            const float dx = xt - s.x, dy = yt - s.y, dz = zt - s.z;
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const float ri = rsqrtf(r2);
-            acc[0] = fmaf(s.w, ri, acc[0]);
-#pragma unroll
-            for (int d = 1; d < ND; ++d) acc[d] = fmaf(tw[d - 1][j], ri, acc[d]);
+            for (int d = 1; d < ND; ++d) acc[u][d] = fmaf(tw[cur][d - 1][j], ri, acc[u][d]);
           }
         }
+      } else {
+#pragma unroll 4
+        for (int j = gi; j < m; j += NG) {
+          const float4 s = tile[cur][j];
 #pragma unroll
-        for (int d = 0; d < ND; ++d) accd[d] += (double)acc[d];
+          for (int u = 0; u < TPT; ++u) {
+            const float dx = xt[u] - s.x, dy = yt[u] - s.y, dz = zt[u] - s.z;
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float ri = rsqrtf(r2);
+            acc[u][0] = fmaf(s.w, ri, acc[u][0]);
+#pragma unroll
+            for (int d = 1; d < ND; ++d) acc[u][d] = fmaf(tw[cur][d - 1][j], ri, acc[u][d]);
+          }
+        }
       }
+#pragma unroll
+      for (int u = 0; u < TPT; ++u)
+#pragma unroll
+        for (int d = 0; d < ND; ++d) two_sum_f(shi[u][d], slo[u][d], acc[u][d]);
+      if (t + 1 < ntiles) store_tile(cur ^ 1);
+      __syncthreads();
     }
   }
 #pragma unroll
-  for (int d = 0; d < ND; ++d) red[d][threadIdx.x] = accd[d];
-  __syncthreads();
-  if (gi == 0 && active) {
-    double near[ND];
+  for (int u = 0; u < TPT; ++u)
 #pragma unroll
-    for (int d = 0; d < ND; ++d) {
-      double s = 0.0;
-      for (int g = 0; g < NG; ++g) s += red[d][g * TP + ti];
-      near[d] = s;
+    for (int d = 0; d < ND; ++d) red[d][u * 128 + threadIdx.x] = make_float2(shi[u][d], slo[u][d]);
+  __syncthreads();
+  if (gi == 0) {
+#pragma unroll
+    for (int u = 0; u < TPT; ++u) {
+      if (!act[u]) continue;
+      double near[ND];
+#pragma unroll
+      for (int d = 0; d < ND; ++d) {
+        float hi = 0.f, lo = 0.f;
+        for (int g = 0; g < NG; ++g) {
+          const float2 v = red[d][u * 128 + g * TS + ts];
+          two_sum_f(hi, lo, v.x);
+          lo += v.y;
+        }
+        near[d] = (double)hi + (double)lo;
+      }
+      const double inv_s = 1.0 / cs.w;
+      l2p_and_store<float, ND>(G, leaf, ndp, loc, xt[u] * inv_s, yt[u] * inv_s, zt[u] * inv_s, near, tr.x + ts + u * TS,
+                               ntp, phi);
     }
-    const double inv_s = 1.0 / cs.w;
-    l2p_and_store<float, ND>(G, leaf, ndp, loc, xt * inv_s, yt * inv_s, zt * inv_s, near, tr.x + ti, ntp, phi);
   }
 }
+
+
 
 template <int ND>
 __global__ void __launch_bounds__(128) k_p2p_l2p_f64(DevGeom G, DevTaskLists L, const double* __restrict__ W,

@@ -70,11 +70,13 @@ def test_fp32_matches_oracle(bc, c1, task):
     assert r2 <= 1e-6, (r2, rm)
 
 
-@pytest.mark.parametrize("prec", ["bf16x2", "bf16x3"])
-@pytest.mark.parametrize("task", ["vtv", "btv"])
+@pytest.mark.parametrize("prec,task", [("bf16x2", "vtv"), ("bf16x2", "vtb"),
+                                       ("bf16x3", "vtv"), ("bf16x3", "vtb"), ("bf16x3", "btv")])
 def test_tensor_core_m2l_matches_oracle(bc, c1, prec, task):
     """tcgen05 M2L (BF16 split, FP32 accumulation, compensated window sums)
-    against O2 at the same p (precision error only) and O1."""
+    against O2 at the same p (precision error only) and O1.  The hi+lo split
+    (16 significant bits per operand) holds 1e-6 for volume sources; surface
+    sources (BtV) need the hi+mid+lo split."""
     m, f, g = c1
     dens = g if task == "btv" else f
     kind = bc.BOUNDARY if task == "btv" else bc.VOLUME
