@@ -315,10 +315,12 @@ __global__ void __launch_bounds__(128) k_p2p_l2p_f32(DevGeom G, DevTaskLists L, 
   split_df(cs.x, chx, clx); split_df(cs.y, chy, cly); split_df(cs.z, chz, clz);
   const int2 tr = G.box_rng[tc][leaf];
   const int nt = tr.y - tr.x;
-  const int slots = (nt + TPT - 1) / TPT;
-  const int TS = slots <= 8 ? 8 : (slots <= 16 ? 16 : (slots <= 32 ? 32 : (slots <= 64 ? 64 : 128)));
+  // TS target slots (TPT targets each) per source group, NG = 128 / TS
+  // groups; threads beyond NG * TS only help loading the tiles
+  const int TS = (nt + TPT - 1) / TPT;
   const int NG = 128 / TS;
-  const int ts = threadIdx.x % TS, gi = threadIdx.x / TS;
+  const int ts = threadIdx.x % TS, gi_raw = threadIdx.x / TS;
+  const int gi = gi_raw < NG ? gi_raw : NG;       // NG: idle for the compute
   float xt[TPT], yt[TPT], zt[TPT];
   bool act[TPT];
 #pragma unroll
@@ -386,8 +388,9 @@ __global__ void __launch_bounds__(128) k_p2p_l2p_f32(DevGeom G, DevTaskLists L, 
       for (int u = 0; u < TPT; ++u)
 #pragma unroll
         for (int d = 0; d < ND; ++d) acc[u][d] = 0.f;
+      const int jstart = gi_raw < NG ? gi : m;        // idle threads skip the loops
       if (rb == r0 && t * kTile < self_len) {
-        for (int j = gi; j < m; j += NG) {
+        for (int j = jstart; j < m; j += NG) {
           const float4 s = tile[cur][j];
 #pragma unroll
           for (int u = 0; u < TPT; ++u) {
@@ -401,7 +404,7 @@ __global__ void __launch_bounds__(128) k_p2p_l2p_f32(DevGeom G, DevTaskLists L, 
         }
       } else {
 #pragma unroll 4
-        for (int j = gi; j < m; j += NG) {
+        for (int j = jstart; j < m; j += NG) {
           const float4 s = tile[cur][j];
 #pragma unroll
           for (int u = 0; u < TPT; ++u) {
@@ -427,7 +430,7 @@ __global__ void __launch_bounds__(128) k_p2p_l2p_f32(DevGeom G, DevTaskLists L, 
 #pragma unroll
     for (int d = 0; d < ND; ++d) red[d][u * 128 + threadIdx.x] = make_float2(shi[u][d], slo[u][d]);
   __syncthreads();
-  if (gi == 0) {
+  if (gi_raw == 0) {
 #pragma unroll
     for (int u = 0; u < TPT; ++u) {
       if (!act[u]) continue;
