@@ -135,6 +135,34 @@ int bcfmm_eval_vtb(bcfmm_ctx* ctx, double* out, int32_t out_is_device);
 int bcfmm_eval_btv(bcfmm_ctx* ctx, double* out, int32_t out_is_device);
 
 /*
+ * Evaluate one task (0 = VtV, 1 = VtB, 2 = BtV) for ONE density without
+ * allocating any memory.  For callers that must not call the CUDA allocator
+ * during evaluation: a host framework that owns and budgets all device
+ * memory itself, or a latency-critical loop where cudaMalloc/cudaFree could
+ * synchronise the device.  The paper has no counterpart; this is a
+ * deployment variant of the tensor-core interaction phase.
+ *   dens_dev  FP64 device array, one P0 value per source element (tets for
+ *             VtV/VtB, triangles for BtV); read on the context's stream
+ *   out_dev   FP64 device array, one value per target element; written
+ *             asynchronously on the context's stream
+ * The tensor-core M2L keeps its per-unit partial sums in a fixed static
+ * device array of 64 MiB (every GPU that loads the library holds it until
+ * the process exits) instead of the context's scratch; all other buffers
+ * are the context's, sized by an earlier bcfmm_set_density (required once).
+ * The first call on a device looks up that array's device address (a
+ * one-time set-up, per device); make that first call before any stream
+ * capture.  Every call on a device shares the array and overwrites it
+ * completely, so nothing carries over between calls, and calls that overlap
+ * on the GPU (different streams or contexts on one device) race on it.
+ * Errors: BCFMM_ERR_ARG (null pointer, bad task, context not built with a
+ * BF16-split precision, or a mesh whose M2L needs more scratch than the
+ * array holds: the message gives both sizes), BCFMM_ERR_STATE (no earlier
+ * bcfmm_set_density, or the current device is not the context's),
+ * BCFMM_ERR_CUDA.
+ */
+int bcfmm_eval_noalloc(bcfmm_ctx* ctx, int32_t task, const double* dens_dev, double* out_dev);
+
+/*
  * Context statistics as one JSON object (points, boxes, levels, list sizes,
  * near pairs, setup seconds, last eval's stage times in ms when timing is
  * on).  Writes at most cap bytes including the terminating NUL.

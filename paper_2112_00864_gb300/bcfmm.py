@@ -22,7 +22,7 @@ PRECISION = {"fp64": 0, "fp32": 1, "bf16x2": 2, "bf16x3": 3}
 VOLUME, BOUNDARY = 0, 1
 EXPORTED = ["bcfmm_default_params", "bcfmm_build_bc_tree", "bcfmm_set_density", "bcfmm_eval_vtv",
             "bcfmm_eval_vtb", "bcfmm_eval_btv", "bcfmm_stats", "bcfmm_last_error", "bcfmm_destroy",
-            "bcfmm_debug_m2l_matrix"]
+            "bcfmm_debug_m2l_matrix", "bcfmm_eval_noalloc"]
 
 
 class Params(C.Structure):
@@ -64,6 +64,8 @@ def load(path: str = LIB_PATH):
         L.bcfmm_destroy.restype = None
         L.bcfmm_debug_m2l_matrix.argtypes = [i32, p, p]
         L.bcfmm_debug_m2l_matrix.restype = C.c_int
+        L.bcfmm_eval_noalloc.argtypes = [p, i32, p, p]
+        L.bcfmm_eval_noalloc.restype = C.c_int
         _lib = L
     return _lib
 
@@ -171,6 +173,13 @@ class Context:
 
     def eval(self, task: str, out=None):
         return {"vtv": self.eval_vtv, "vtb": self.eval_vtb, "btv": self.eval_btv}[task](out)
+
+    def eval_noalloc(self, task: str, dens, out):
+        """One task for one density with no allocation (device tensors)."""
+        t = {"vtv": 0, "vtb": 1, "btv": 2}[task]
+        assert dens.is_cuda and out.is_cuda and dens.dtype == out.dtype and dens.element_size() == 8
+        _check(self._lib.bcfmm_eval_noalloc(self._ctx, t, C.c_void_p(dens.data_ptr()), C.c_void_p(out.data_ptr())))
+        return out
 
     def stats(self) -> dict:
         buf = C.create_string_buffer(1 << 16)

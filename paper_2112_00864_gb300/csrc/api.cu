@@ -609,6 +609,57 @@ extern "C" int bcfmm_eval_vtv(bcfmm_ctx* C, double* out, int32_t d) { return eva
 extern "C" int bcfmm_eval_vtb(bcfmm_ctx* C, double* out, int32_t d) { return eval_impl(C, 1, out, d); }
 extern "C" int bcfmm_eval_btv(bcfmm_ctx* C, double* out, int32_t d) { return eval_impl(C, 2, out, d); }
 
+// One task, one density, no allocation: the tensor-core M2L writes its unit
+// partial sums into the library's fixed static device array instead of the
+// context's scratch; every other buffer was sized by an earlier
+// bcfmm_set_density.  Nothing here calls cudaMalloc, cudaFree or an
+// allocating library routine.
+extern "C" int bcfmm_eval_noalloc(bcfmm_ctx* C, int32_t task, const double* dens_dev, double* out_dev) {
+  if (!C) return fail(BCFMM_ERR_ARG, "eval_noalloc: null context");
+  if (task < 0 || task > 2) return fail(BCFMM_ERR_ARG, "eval_noalloc: task must be 0 (VtV), 1 (VtB) or 2 (BtV)");
+  if (!dens_dev || !out_dev) return fail(BCFMM_ERR_ARG, "eval_noalloc: null density or output");
+  if (C->prm.precision != BCFMM_FP32_BF16X2 && C->prm.precision != BCFMM_FP32_BF16X3)
+    return fail(BCFMM_ERR_ARG, "eval_noalloc: needs a context built with a BF16-split (tensor-core) precision");
+  TaskDev& D = C->task[task];
+  const DevTaskLists& L = D.L;
+  const int kind = L.src_cls;
+  if (C->work_ndp < 1 || C->tc_momb == nullptr)
+    return fail(BCFMM_ERR_STATE, "eval_noalloc: call bcfmm_set_density once first (it sizes the work buffers)");
+  int dev = -1;
+  CU(cudaGetDevice(&dev));
+  if (dev != C->device) return fail(BCFMM_ERR_STATE, "eval_noalloc: the context's device is not the current device");
+  float2* partial = nullptr;
+  size_t cap = 0;
+  CU(m2l_tc_noalloc_scratch(dev, &partial, &cap));
+  const size_t need = (size_t)L.tc_nunit * C->tc.npad * 128;
+  if (need > cap)
+    return fail(BCFMM_ERR_ARG, "eval_noalloc: the mesh needs " + std::to_string(need * sizeof(float2)) +
+                                   " bytes of M2L scratch, more than the fixed " + std::to_string(cap * sizeof(float2)) +
+                                   " bytes (use bcfmm_eval_vtv/vtb/btv)");
+  cudaStream_t st = C->st;
+  const DevGeom& G = C->G;
+  const int ndp = 1;
+  const int64_t nsp = C->npts[L.src_cls], ntp = C->npts[L.tgt_cls];
+  const int64_t nsel = kind == 0 ? C->ntet : C->ntri;
+  const size_t nexp = (size_t)C->nbox * ndp * C->G.ms;
+  CU(launch_weights<float>(G, L.src_cls, nsp, dens_dev, nsel, 1, ndp, C->W32, st));
+  CU(cudaMemsetAsync(C->mom32, 0, nexp * sizeof(float), st));
+  CU(cudaMemsetAsync(C->loc32, 0, nexp * sizeof(float), st));
+  CU(launch_p2m<float>(G, L, C->W32, nsp, ndp, C->mom32, st));
+  for (int l = C->nlevels - 1; l >= 0; --l) {
+    const int n = D.m2m_off[l + 1] - D.m2m_off[l];
+    CU(launch_m2m<float>(G, D.m2m_parent + D.m2m_off[l], n, C->M2M32, ndp, C->mom32, st));
+  }
+  CU(launch_m2l_tc(G, L, C->tc, ndp, C->mom32, C->loc32, partial, C->tc_momb, st));
+  for (int l = 3; l < C->nlevels; ++l) {
+    const int n = D.l2l_off[l + 1] - D.l2l_off[l];
+    CU(launch_l2l<float>(G, D.l2l_child + D.l2l_off[l], n, C->L2L32, ndp, C->loc32, st));
+  }
+  CU(launch_p2p_l2p_f32(G, L, C->W32, nsp, ntp, ndp, C->loc32, C->phi, st));
+  CU(launch_elem_sum(G, L, C->phi, ntp, dens_dev, 1, out_dev, st));
+  return BCFMM_OK;
+}
+
 extern "C" int bcfmm_stats(const bcfmm_ctx* C, char* json, size_t cap) {
   if (!C || !json) return fail(BCFMM_ERR_ARG, "stats: null argument");
   std::string s = "{";

@@ -33,6 +33,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "internal.h"
@@ -663,5 +664,34 @@ cudaError_t launch_m2l_tc(const DevGeom& G, const DevTaskLists& L, const M2LTens
 
 int m2l_tc_smem_bytes(int p, int nsplit) { return make_plan(p, nsplit).smem_bytes; }
 int m2l_tc_npad(int p) { return make_plan(p, 2).npad; }
+
+// ------------------------------------------------ fixed scratch (no alloc)
+// Unit partial sums for bcfmm_eval_noalloc: a file-scope device array, so
+// that entry point needs no cudaMalloc.  Every device that loads this
+// library holds it (64 MiB) until the process exits.  Calls that use it
+// and overlap on the GPU race on it; each unit writes all of its entries
+// before the reduce reads them, so nothing needs clearing between calls.
+static __device__ __align__(256) float2 g_noalloc_partial[kNoAllocPartialElems];
+
+namespace {
+std::mutex g_noalloc_mu;
+float2* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+}  // namespace
+
+cudaError_t m2l_tc_noalloc_scratch(int device, float2** ptr, size_t* elems) {
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (device < 0 || device >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
+  if (g_noalloc_ptr[device] == nullptr) {
+    // host code only knows a stand-in for the array: ask the runtime for
+    // its device address, once per device, with that device current
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partial);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[device] = static_cast<float2*>(p);
+  }
+  *ptr = g_noalloc_ptr[device];
+  *elems = kNoAllocPartialElems;
+  return cudaSuccess;
+}
 
 }  // namespace bcfmm

@@ -25,6 +25,12 @@ cudaError_t m2l_tc_prepare_tables(int p, int ncode, const double* T /*[ncode][np
 cudaError_t launch_m2l_tc(const DevGeom& G, const DevTaskLists& L, const M2LTensorTables& tab, int ndp,
                           const float* mom, float* loc, float2* partial, void* momb, cudaStream_t st);
 int m2l_tc_npad(int p);
+
+// Fixed device scratch for the unit partial sums of bcfmm_eval_noalloc
+// (float2 elements); the address is looked up once per device.
+constexpr size_t kNoAllocPartialElems = size_t(8) << 20;   // 64 MiB
+constexpr int kNoAllocMaxDevices = 64;
+cudaError_t m2l_tc_noalloc_scratch(int device, float2** ptr, size_t* elems);
 void m2l_tc_free_tables(M2LTensorTables* t);
 
 }  // namespace bcfmm
