@@ -22,7 +22,7 @@
 // offsets; a finished window is added into a compensated running sum SH + SL
 // (TwoSum, in TMEM) one window later, so the ~10^3-term sum of a box never
 // runs through one long FP32 chain.  Each unit writes its (SH, SL) partial;
-// k_m2l_tc_reduce adds the partials of a tile in a fixed order
+// k_m2l_unit_reduce adds the partials of a tile in a fixed order
 // (deterministic) and applies the 1/s scaling.
 //
 // Shared-memory operands use the K-major, no-swizzle canonical layout: core
@@ -505,7 +505,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(TcArgs args) {
 
 // lambda[tgt][a] = (sum over the tile's units of SH + SL) / s, in unit order
 template <int NPAD>
-__global__ void __launch_bounds__(kTileM) k_m2l_tc_reduce(const int* __restrict__ tile_tgt,
+__global__ void __launch_bounds__(kTileM) k_m2l_unit_reduce(const int* __restrict__ tile_tgt,
                                                           const int* __restrict__ tile_unit_off,
                                                           const float2* __restrict__ partial, int nunit, int ndp,
                                                           int np, int ms, const double4_32a* __restrict__ box_cs,
@@ -598,7 +598,7 @@ static cudaError_t launch_ns(const TcArgs& a, int ndp, cudaStream_t st) {
 template <int NPAD>
 static cudaError_t launch_reduce(const DevGeom& G, const DevTaskLists& L, const float2* partial, int ndp, float* loc,
                                  cudaStream_t st) {
-  k_m2l_tc_reduce<NPAD><<<dim3(L.tc_ntile, ndp), kTileM, 0, st>>>(L.tc_tile_tgt, L.tc_tile_unit_off, partial,
+  k_m2l_unit_reduce<NPAD><<<dim3(L.tc_ntile, ndp), kTileM, 0, st>>>(L.tc_tile_tgt, L.tc_tile_unit_off, partial,
                                                                   L.tc_nunit, ndp, G.np, G.ms, G.box_cs, loc);
   return cudaGetLastError();
 }
