@@ -84,6 +84,20 @@ typedef struct {
                            of two same-level box centres (Eq. def:neighbors applied to
                            boxes); default 0.5 as in Sec. 5; values in (0.866, 1] give the
                            27 boxes whose closures touch; range 0.3..1                  */
+  int32_t tc_unit;      /* tensor-core M2L: interaction entries per work unit (one CTA);
+                           0 = automatic (about 4 units per SM); 1..4096               */
+  int32_t near_mode;    /* near-singular pairs (near pairs whose closures are apart):
+                           0 = near rule in FP64 like every near pair (default);
+                           1 = learned correction (bcfmm_mlp_* below) wherever the
+                               network's calibrated error is <= mlp_tol, the FP64 near
+                               rule elsewhere;
+                           2 = no correction: product rule only (the reference point
+                               the learned correction is measured against)             */
+  double mlp_tol;       /* near_mode 1: largest accepted calibrated error of one pair's
+                           correction, relative to the pair's product-rule value; 1e-3 */
+  const void* mlp_blob; /* near_mode 1: trained network and calibration, format of
+                           bcfmm_mlp_blob_size(); read during the build only           */
+  int64_t mlp_blob_bytes;
 } bcfmm_params;
 
 /* Fills *prm with the defaults above.  Never fails. */
@@ -107,6 +121,44 @@ int bcfmm_build_bc_tree(const double* verts, int64_t nvert,
                         const int32_t* tets, int64_t ntet,
                         const int32_t* tris, int64_t ntri,
                         const bcfmm_params* prm, void* stream, bcfmm_ctx** out);
+
+/*
+ * Build one context for a batch of nmesh independent meshes (the paper
+ * treats one mesh at a time; a batch is that computation for every mesh,
+ * with no interaction between meshes).  Each mesh gets its own octree,
+ * lists and near pairs exactly as bcfmm_build_bc_tree would build them;
+ * the library then concatenates them into one forest so that every stage
+ * of an evaluation is one launch over all meshes.
+ *   verts     [vert_off[nmesh]][3] FP64, mesh m's vertices at rows
+ *             vert_off[m] .. vert_off[m+1]-1
+ *   tets      [tet_off[nmesh]][4] int32 vertex ids LOCAL to the mesh
+ *   tris      [tri_off[nmesh]][3] int32 local vertex ids (may be NULL when
+ *             tri_off[nmesh] == 0)
+ *   vert_off, tet_off, tri_off  [nmesh+1] prefix sums starting at 0; every
+ *             mesh has >= 1 vertex and >= 1 tet, triangles may be absent
+ * All arrays are host memory.  Densities and outputs of the context are
+ * the concatenation over meshes: [ndens][tet_off[nmesh]] for volume
+ * quantities, [ndens][tri_off[nmesh]] for boundary ones, mesh m's
+ * elements at columns tet_off[m] .. tet_off[m+1]-1 (tri_off likewise).
+ * Errors as bcfmm_build_bc_tree; the message names the failing mesh.
+ */
+int bcfmm_build_batch(const double* verts, const int64_t* vert_off,
+                      const int32_t* tets, const int64_t* tet_off,
+                      const int32_t* tris, const int64_t* tri_off, int32_t nmesh,
+                      const bcfmm_params* prm, void* stream, bcfmm_ctx** out);
+
+/*
+ * Build a context on the same meshes as `base` with other tree, expansion
+ * or precision parameters (p, leaf_size, eta0, precision, tc_unit, timing).
+ * The near pairs and their corrections do not depend on those parameters
+ * and are copied from `base` on the device instead of being recomputed, so
+ * an autotuner can try many configurations for the price of the tree and
+ * list builds.  eta_ns, near_n, near_k and near_mode must equal base's.
+ * The new context uses base's stream; base stays valid and independent.
+ * Errors: BCFMM_ERR_ARG (mismatching near-pair parameters), BCFMM_ERR_STATE
+ * (base's device is not current), as bcfmm_build_bc_tree otherwise.
+ */
+int bcfmm_build_like(const bcfmm_ctx* base, const bcfmm_params* prm, bcfmm_ctx** out);
 
 /*
  * Set the P0 density coefficients (one value per element, Sec. 1.2).
@@ -135,6 +187,25 @@ int bcfmm_eval_vtb(bcfmm_ctx* ctx, double* out, int32_t out_is_device);
 int bcfmm_eval_btv(bcfmm_ctx* ctx, double* out, int32_t out_is_device);
 
 /*
+ * Evaluate the tasks in task_mask (bit 0 VtV, bit 1 VtB, bit 2 BtV) as one
+ * CUDA graph launch on the context's stream (the paper evaluates tasks one
+ * by one; the graph removes the per-kernel launch overhead of the many
+ * small per-level stages).  Outputs as in bcfmm_eval_*, device memory only;
+ * a pointer whose bit is clear is ignored.  When VtV and VtB are both in
+ * the mask, VtB reuses VtV's weights and upward pass (same density).
+ * The first call for a given (mask, output pointers, density counts, work
+ * buffers) combination captures and instantiates the graph on a stream the
+ * library owns (this allocates); later calls with the same combination
+ * only launch it.  Densities may change between calls through
+ * bcfmm_set_density (the graph reads the context's density buffer).
+ * Expired bounded device waits are reported through bcfmm_stats
+ * ("device_error"), not by this call.
+ * Errors: BCFMM_ERR_ARG (mask, null output), BCFMM_ERR_STATE (density not
+ * set), BCFMM_ERR_CUDA (capture or instantiation failed).
+ */
+int bcfmm_eval_graph(bcfmm_ctx* ctx, int32_t task_mask, double* out_vtv, double* out_vtb, double* out_btv);
+
+/*
  * Evaluate one task (0 = VtV, 1 = VtB, 2 = BtV) for ONE density without
  * allocating any memory.  For callers that must not call the CUDA allocator
  * during evaluation: a host framework that owns and budgets all device
@@ -161,6 +232,19 @@ int bcfmm_eval_btv(bcfmm_ctx* ctx, double* out, int32_t out_is_device);
  * BCFMM_ERR_CUDA.
  */
 int bcfmm_eval_noalloc(bcfmm_ctx* ctx, int32_t task, const double* dens_dev, double* out_dev);
+
+/*
+ * The discrete operator itself, summed pair by pair in FP64 on the GPU for
+ * the target elements targets[0..n): every source quadrature point with
+ * the product rule (r = 0 skipped) plus the element's near corrections,
+ * no expansions.  It is the reference the fast evaluation approximates,
+ * at O(n * #source points) cost; the autotuner measures errors against it.
+ *   targets  host int64 [n] element indices of the task's target kind, n <= 2^20
+ *   out      host FP64 [ndens][n]; the call synchronises the stream
+ * Errors: BCFMM_ERR_ARG (index out of range), BCFMM_ERR_STATE (density
+ * not set), BCFMM_ERR_CUDA.
+ */
+int bcfmm_direct_sample(bcfmm_ctx* ctx, int32_t task, const int64_t* targets, int64_t n, double* out);
 
 /*
  * Context statistics as one JSON object (points, boxes, levels, list sizes,

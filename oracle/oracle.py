@@ -34,7 +34,10 @@ def build_lib(force: bool = False) -> str:
     newest = max(os.path.getmtime(s) for s in _SRC)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < newest:
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-        cmd = ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-std=c11", "-o", tmp] + _SRC + ["-lm"]
+        # -ffp-contract=off: every product and sum rounds as written, so the
+        # quadrature points (and the octree built on them) do not depend on
+        # whether the host compiler fuses multiply-adds (it does on aarch64)
+        cmd = ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-std=c11", "-ffp-contract=off", "-o", tmp] + _SRC + ["-lm"]
         subprocess.check_call(cmd)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH

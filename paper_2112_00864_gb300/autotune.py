@@ -1,0 +1,117 @@
+"""Autotuner: pick the fastest evaluation configuration that meets an
+accuracy target on the caller's own meshes and densities.
+
+Search space (all of it is cheap to try because ``Context.build_like``
+copies the near pairs and their FP64 corrections instead of recomputing
+them): leaf size, expansion order p with the precision the tensor-core
+M2L allows for it (BF16 hi+lo split for p <= 7, FP32 on CUDA cores above),
+and the tensor-core work-unit size ("tile" of the M2L launch: interaction
+entries per CTA).  Each candidate is timed with CUDA events as the graph
+launch a user makes (``Context.eval_graph``) and its error is measured on
+sampled target elements against the library's FP64 direct evaluation of
+the discrete operator (``Context.direct_sample``), as the relative L2
+error of cell averages.  The winner is the fastest candidate whose error
+is at most ``tol`` for every task.
+"""
+from __future__ import annotations
+
+import itertools
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import bcfmm
+
+DEFAULT_SPACE = dict(leaf_size=(32, 64, 128), p=(4, 6, 8), tc_unit=(0, 32))
+
+
+@dataclass
+class Trial:
+    params: dict
+    ms: float = float("nan")
+    err: dict = field(default_factory=dict)
+    ok: bool = False
+    note: str = ""
+
+
+def _precision_for(p: int) -> str:
+    return "bf16x2" if p <= 7 else "fp32"
+
+
+def candidates(space: dict | None = None):
+    space = dict(DEFAULT_SPACE, **(space or {}))
+    out = []
+    for ls, p in itertools.product(space["leaf_size"], space["p"]):
+        prec = _precision_for(p)
+        units = space["tc_unit"] if prec.startswith("bf16") else (0,)
+        for u in units:
+            out.append(dict(leaf_size=int(ls), p=int(p), precision=prec, tc_unit=int(u)))
+    return out
+
+
+def _cell_sizes(ctx, task: str) -> np.ndarray:
+    if task == "vtb":
+        v = ctx.element_vertices(bcfmm.BOUNDARY)
+        return 0.5 * np.linalg.norm(np.cross(v[:, 1] - v[:, 0], v[:, 2] - v[:, 0]), axis=1)
+    v = ctx.element_vertices(bcfmm.VOLUME)
+    return np.abs(np.einsum("ij,ij->i", np.cross(v[:, 1] - v[:, 0], v[:, 2] - v[:, 0]), v[:, 3] - v[:, 0])) / 6.0
+
+
+def _time_graph(ctx, tasks, outs, reps: int) -> float:
+    import torch
+    st = torch.cuda.current_stream()
+    outs = ctx.eval_graph(tasks, outs)                  # capture
+    for _ in range(2):
+        ctx.eval_graph(tasks, outs)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * reps)]
+    ms = []
+    for r in range(reps):
+        ev[2 * r].record(st)
+        ctx.eval_graph(tasks, outs)
+        ev[2 * r + 1].record(st)
+    torch.cuda.synchronize()
+    for r in range(reps):
+        ms.append(ev[2 * r].elapsed_time(ev[2 * r + 1]))
+    return float(np.median(ms))
+
+
+def autotune(base: "bcfmm.Context", dens_volume, dens_boundary=None, tasks=("vtv", "vtb"), tol: float = 1e-6,
+             space: dict | None = None, nsample: int = 64, reps: int = 5, seed: int = 0, verbose: bool = False):
+    """Returns (best params dict, list of Trial).  ``base`` is any context on
+    the meshes (its near pairs are reused); densities as for set_density."""
+    rng = np.random.default_rng(seed)
+    base.set_density(bcfmm.VOLUME, dens_volume)
+    if dens_boundary is not None:
+        base.set_density(bcfmm.BOUNDARY, dens_boundary)
+    refs = {}
+    for t in tasks:
+        n = base.ntri if t == "vtb" else base.ntet
+        idx = np.sort(rng.choice(n, size=min(nsample, n), replace=False))
+        size = _cell_sizes(base, t)[idx]
+        refs[t] = (idx, base.direct_sample(t, idx) / size, size)
+    trials = []
+    for cand in candidates(space):
+        tr = Trial(params=cand)
+        try:
+            ctx = base.build_like(**cand)
+            ctx.set_density(bcfmm.VOLUME, dens_volume)
+            if dens_boundary is not None:
+                ctx.set_density(bcfmm.BOUNDARY, dens_boundary)
+            tr.ms = _time_graph(ctx, tasks, None, reps)
+            outs = ctx.eval_graph(tasks)
+            for t in tasks:
+                idx, ref, size = refs[t]
+                u = outs[t].cpu().numpy()[:, idx] / size
+                tr.err[t] = float(np.linalg.norm(u - ref) / np.linalg.norm(ref))
+            tr.ok = all(e <= tol for e in tr.err.values())
+            ctx.close()
+        except bcfmm.BcfmmError as ex:
+            tr.note = str(ex)
+        if verbose:
+            print(f"autotune {cand} ms={tr.ms:.3f} err={tr.err} ok={tr.ok} {tr.note}", flush=True)
+        trials.append(tr)
+    good = [t for t in trials if t.ok]
+    if not good:
+        raise RuntimeError(f"autotune: no configuration reaches tol={tol:g}")
+    best = min(good, key=lambda t: t.ms)
+    return dict(best.params), trials

@@ -22,12 +22,16 @@ PRECISION = {"fp64": 0, "fp32": 1, "bf16x2": 2, "bf16x3": 3}
 VOLUME, BOUNDARY = 0, 1
 EXPORTED = ["bcfmm_default_params", "bcfmm_build_bc_tree", "bcfmm_set_density", "bcfmm_eval_vtv",
             "bcfmm_eval_vtb", "bcfmm_eval_btv", "bcfmm_stats", "bcfmm_last_error", "bcfmm_destroy",
-            "bcfmm_debug_m2l_matrix", "bcfmm_eval_noalloc"]
+            "bcfmm_debug_m2l_matrix", "bcfmm_eval_noalloc", "bcfmm_build_batch", "bcfmm_eval_graph",
+            "bcfmm_build_like", "bcfmm_direct_sample"]
+TASK_BIT = {"vtv": 1, "vtb": 2, "btv": 4}
 
 
 class Params(C.Structure):
     _fields_ = [("p", C.c_int32), ("leaf_size", C.c_int32), ("eta_ns", C.c_double), ("near_n", C.c_int32),
-                ("near_k", C.c_int32), ("precision", C.c_int32), ("timing", C.c_int32), ("eta0", C.c_double)]
+                ("near_k", C.c_int32), ("precision", C.c_int32), ("timing", C.c_int32), ("eta0", C.c_double),
+                ("tc_unit", C.c_int32), ("near_mode", C.c_int32), ("mlp_tol", C.c_double), ("mlp_blob", C.c_void_p),
+                ("mlp_blob_bytes", C.c_int64)]
 
 
 class BcfmmError(RuntimeError):
@@ -66,6 +70,14 @@ def load(path: str = LIB_PATH):
         L.bcfmm_debug_m2l_matrix.restype = C.c_int
         L.bcfmm_eval_noalloc.argtypes = [p, i32, p, p]
         L.bcfmm_eval_noalloc.restype = C.c_int
+        L.bcfmm_build_batch.argtypes = [p, p, p, p, p, p, i32, C.POINTER(Params), p, C.POINTER(p)]
+        L.bcfmm_build_batch.restype = C.c_int
+        L.bcfmm_eval_graph.argtypes = [p, i32, p, p, p]
+        L.bcfmm_eval_graph.restype = C.c_int
+        L.bcfmm_build_like.argtypes = [p, C.POINTER(Params), C.POINTER(p)]
+        L.bcfmm_build_like.restype = C.c_int
+        L.bcfmm_direct_sample.argtypes = [p, i32, p, i64, p]
+        L.bcfmm_direct_sample.restype = C.c_int
         _lib = L
     return _lib
 
@@ -104,10 +116,16 @@ def _ptr(x):
 
 
 class Context:
-    """One mesh on the current CUDA device, bound to ``stream`` (a
-    torch.cuda.Stream, an int handle, or None for the current torch stream)."""
+    """One mesh, or a batch of independent meshes, on the current CUDA
+    device, bound to ``stream`` (a torch.cuda.Stream, an int handle, or None
+    for the current torch stream).
 
-    def __init__(self, verts, tets, tris, params: Params | None = None, stream=None, **kw):
+    ``Context(verts, tets, tris)`` builds one mesh; ``Context.from_meshes``
+    builds a batch whose densities and outputs are the concatenation of the
+    meshes' element columns (``tet_off`` / ``tri_off`` give the ranges)."""
+
+    def __init__(self, verts, tets, tris, params: Params | None = None, stream=None, *, vert_off=None,
+                 tet_off=None, tri_off=None, **kw):
         import torch
         self._lib = load()
         self.params = params if params is not None else default_params(**kw)
@@ -120,11 +138,74 @@ class Context:
         self._f = np.ascontiguousarray(tris, np.int32) if tris is not None else np.zeros((0, 3), np.int32)
         self.ntet, self.ntri = self._t.shape[0], self._f.shape[0]
         ctx = C.c_void_p()
-        _check(self._lib.bcfmm_build_bc_tree(self._v.ctypes.data, self._v.shape[0], self._t.ctypes.data, self.ntet,
-                                             self._f.ctypes.data, self.ntri, C.byref(self.params),
-                                             C.c_void_p(handle), C.byref(ctx)))
+        self.vert_off = np.array([0, self._v.shape[0]], np.int64) if vert_off is None else \
+            np.ascontiguousarray(vert_off, np.int64)
+        if vert_off is None:
+            self.nmesh = 1
+            self.tet_off = np.array([0, self.ntet], np.int64)
+            self.tri_off = np.array([0, self.ntri], np.int64)
+            _check(self._lib.bcfmm_build_bc_tree(self._v.ctypes.data, self._v.shape[0], self._t.ctypes.data,
+                                                 self.ntet, self._f.ctypes.data, self.ntri, C.byref(self.params),
+                                                 C.c_void_p(handle), C.byref(ctx)))
+        else:
+            vo = np.ascontiguousarray(vert_off, np.int64)
+            self.tet_off = np.ascontiguousarray(tet_off, np.int64)
+            self.tri_off = np.ascontiguousarray(tri_off, np.int64)
+            self.nmesh = len(vo) - 1
+            assert len(self.tet_off) == len(self.tri_off) == len(vo)
+            _check(self._lib.bcfmm_build_batch(self._v.ctypes.data, vo.ctypes.data, self._t.ctypes.data,
+                                               self.tet_off.ctypes.data, self._f.ctypes.data,
+                                               self.tri_off.ctypes.data, self.nmesh, C.byref(self.params),
+                                               C.c_void_p(handle), C.byref(ctx)))
         self._ctx = ctx
         self.ndens = {VOLUME: 0, BOUNDARY: 0}
+
+    @classmethod
+    def from_meshes(cls, meshes, **kw):
+        """Batch of independent meshes (objects with verts, tets, tris)."""
+        vo, to, ro = [0], [0], [0]
+        for m in meshes:
+            vo.append(vo[-1] + len(m.verts))
+            to.append(to[-1] + len(m.tets))
+            ro.append(ro[-1] + len(m.tris))
+        verts = np.concatenate([np.asarray(m.verts, np.float64) for m in meshes])
+        tets = np.concatenate([np.asarray(m.tets, np.int32) for m in meshes])
+        tris = np.concatenate([np.asarray(m.tris, np.int32).reshape(-1, 3) for m in meshes])
+        return cls(verts, tets, tris, vert_off=vo, tet_off=to, tri_off=ro, **kw)
+
+    def build_like(self, **overrides) -> "Context":
+        """New context on the same meshes with other tree / precision
+        parameters (p, leaf_size, eta0, precision, tc_unit); the near pairs and
+        their corrections are copied from this context, not recomputed."""
+        new = object.__new__(Context)
+        new._lib = self._lib
+        prm = Params()
+        C.pointer(prm)[0] = self.params
+        for k, v in overrides.items():
+            if k == "precision" and isinstance(v, str):
+                v = PRECISION[v]
+            setattr(prm, k, v)
+        new.params = prm
+        new.stream = self.stream
+        new._v, new._t, new._f = self._v, self._t, self._f
+        new.ntet, new.ntri, new.nmesh = self.ntet, self.ntri, self.nmesh
+        new.tet_off, new.tri_off, new.vert_off = self.tet_off, self.tri_off, self.vert_off
+        ctx = C.c_void_p()
+        new._ctx = None
+        _check(self._lib.bcfmm_build_like(self._ctx, C.byref(prm), C.byref(ctx)))
+        new._ctx = ctx
+        new.ndens = {VOLUME: 0, BOUNDARY: 0}
+        return new
+
+    def direct_sample(self, task: str, targets) -> np.ndarray:
+        """FP64 direct evaluation (no expansions) of the target elements
+        ``targets`` on the GPU: [ndens, len(targets)] host array."""
+        t = {"vtv": 0, "vtb": 1, "btv": 2}[task]
+        kind = BOUNDARY if task == "btv" else VOLUME
+        tg = np.ascontiguousarray(targets, np.int64)
+        out = np.zeros((self.ndens[kind], len(tg)))
+        _check(self._lib.bcfmm_direct_sample(self._ctx, t, tg.ctypes.data, len(tg), out.ctypes.data))
+        return out
 
     @classmethod
     def from_mesh(cls, mesh, **kw):
@@ -180,6 +261,38 @@ class Context:
         assert dens.is_cuda and out.is_cuda and dens.dtype == out.dtype and dens.element_size() == 8
         _check(self._lib.bcfmm_eval_noalloc(self._ctx, t, C.c_void_p(dens.data_ptr()), C.c_void_p(out.data_ptr())))
         return out
+
+    def eval_graph(self, tasks=("vtv", "vtb"), outs=None):
+        """Evaluate ``tasks`` as one CUDA graph launch (captured on first use
+        for this set of tasks and output buffers).  Returns {task: tensor}."""
+        import torch
+        outs = dict(outs or {})
+        mask = 0
+        ptrs = [None, None, None]
+        for i, t in enumerate(("vtv", "vtb", "btv")):
+            if t not in tasks:
+                continue
+            mask |= TASK_BIT[t]
+            kind = BOUNDARY if t == "btv" else VOLUME
+            nel = self.ntri if t == "vtb" else self.ntet
+            if t not in outs:
+                outs[t] = torch.empty((self.ndens[kind], nel), dtype=torch.float64, device="cuda")
+            assert outs[t].is_cuda and outs[t].is_contiguous()
+            ptrs[i] = C.c_void_p(outs[t].data_ptr())
+        _check(self._lib.bcfmm_eval_graph(self._ctx, mask, *ptrs))
+        return outs
+
+    def element_vertices(self, kind: int) -> np.ndarray:
+        """[n, 4 or 3, 3] vertex coordinates of the volume / boundary elements
+        (mesh-local vertex ids of a batch resolved)."""
+        el, off = (self._t, self.tet_off) if kind == VOLUME else (self._f, self.tri_off)
+        shift = np.repeat(self.vert_off[:-1], np.diff(off))
+        return self._v[el + shift[:, None]]
+
+    def split(self, out, kind_or_task):
+        """Per-mesh views of a batch output / density ([ndens][n] -> list)."""
+        off = self.tri_off if kind_or_task in ("vtb", BOUNDARY) else self.tet_off
+        return [out[..., off[m]:off[m + 1]] for m in range(self.nmesh)]
 
     def stats(self) -> dict:
         buf = C.create_string_buffer(1 << 16)

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libbcfmm.so")
-SOURCES = ["api.cu", "kernels_fmm.cu", "kernels_near.cu", "m2l_tc.cu", "setup.cpp"]
+SOURCES = ["api.cu", "kernels_fmm.cu", "kernels_near.cu", "kernels_aux.cu", "m2l_tc.cu", "setup.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -28,7 +28,10 @@ def nvcc() -> str:
 
 
 def _flags(src: str):
-    common = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC,-fopenmp,-O3", "-I", os.path.join(ROOT, "include")]
+    # host code: -ffp-contract=off keeps the FP64 setup (quadrature points,
+    # octree decisions) independent of multiply-add fusion, the same on
+    # x86_64 and aarch64
+    common = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC,-fopenmp,-O3,-ffp-contract=off", "-I", os.path.join(ROOT, "include")]
     if src.endswith(".cu"):
         # -ftz=true: no operand of the FP32 passes comes near the denormal
         # range, and it lets rsqrtf compile to the bare MUFU reciprocal root

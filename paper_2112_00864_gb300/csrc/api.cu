@@ -98,12 +98,29 @@ struct bcfmm_ctx {
   double *W64 = nullptr, *mom64 = nullptr, *loc64 = nullptr, *phi = nullptr, *out_dev = nullptr;
   float *W32 = nullptr, *mom32 = nullptr, *loc32 = nullptr;
   // stats
+  int nmesh = 1;
+  std::vector<int64_t> mesh_tet_off, mesh_tri_off;
+  // host copy of the input meshes (bcfmm_build_like rebuilds from it)
+  std::vector<double> h_verts;
+  std::vector<int32_t> h_tets, h_tris;
+  std::vector<int64_t> h_vo, h_to, h_ro;
+  const bcfmm_ctx* reuse = nullptr;    // during a build: context whose near pairs are copied
+  double sec_host = 0;
   double sec_setup = 0, sec_tree = 0, sec_lists = 0, sec_near_host = 0, sec_near_dev = 0;
   std::vector<int> leaves_per_level, boxes_per_level;
   // per task: CUDA events around the stages of the last evaluation; elapsed
   // times are read lazily by bcfmm_stats (no host sync inside an eval)
   cudaEvent_t ev[3][8] = {};
   bool ev_ok = false, ev_rec[3] = {false, false, false};
+  // CUDA graph of bcfmm_eval_graph
+  struct {
+    cudaGraphExec_t exec = nullptr;
+    int mask = 0, work_gen = -1, ndens[2] = {0, 0};
+    double* out[3] = {nullptr, nullptr, nullptr};
+    int nodes = 0;
+  } graph;
+  cudaStream_t cap_st = nullptr;
+  int work_gen = 0;                    // bumped whenever the work buffers move
 };
 
 static double wall() {
@@ -126,6 +143,11 @@ extern "C" void bcfmm_default_params(bcfmm_params* prm) {
   prm->precision = BCFMM_FP64;
   prm->timing = 0;
   prm->eta0 = 0.5;
+  prm->tc_unit = 0;
+  prm->near_mode = 0;
+  prm->mlp_tol = 1e-3;
+  prm->mlp_blob = nullptr;
+  prm->mlp_blob_bytes = 0;
 }
 
 extern "C" const char* bcfmm_last_error(void) { return g_err.c_str(); }
@@ -212,7 +234,7 @@ static int upload_task(bcfmm_ctx* C, const HostSetup& H, int t) {
     int nsm = 152;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, C->device);
     const int64_t E = D.tc_entries;
-    const int U = (int)std::max<int64_t>(8, (E + 4 * nsm - 1) / (4 * nsm));
+    const int U = C->prm.tc_unit > 0 ? C->prm.tc_unit : (int)std::max<int64_t>(8, (E + 4 * nsm - 1) / (4 * nsm));
     std::vector<int4> units;
     std::vector<int> tile_unit_off(1, 0);
     for (int tl = 0; tl < L.tc_ntile; ++tl) {
@@ -234,6 +256,19 @@ static int upload_task(bcfmm_ctx* C, const HostSetup& H, int t) {
   int64_t *cor_off;
   int *cor_col, *cor_row;
   double* cor_val;
+  if (C->reuse) {
+    // same meshes and near-pair parameters: the CSR and its FP64 values
+    // do not depend on the tree, copy them
+    const TaskDev& B = C->reuse->task[t];
+    D.nnz = B.nnz;
+    CU(m.alloc(&cor_off, nte + 1));
+    CU(m.alloc(&cor_col, D.nnz));
+    CU(m.alloc(&cor_val, D.nnz));
+    CU(cudaMemcpyAsync(cor_off, B.L.cor_off, (nte + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
+    CU(cudaMemcpyAsync(cor_col, B.L.cor_col, D.nnz * sizeof(int), cudaMemcpyDeviceToDevice, st));
+    CU(cudaMemcpyAsync(cor_val, B.L.cor_val, D.nnz * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    L.cor_off = cor_off; L.cor_col = cor_col; L.cor_val = cor_val;
+  } else {
   D.nnz = (int64_t)T.cor_col.size();
   CU(m.upload(&cor_off, T.cor_off.data(), T.cor_off.size(), st));
   CU(m.upload(&cor_col, T.cor_col.data(), T.cor_col.size(), st));
@@ -264,6 +299,7 @@ static int upload_task(bcfmm_ctx* C, const HostSetup& H, int t) {
                     (void*)cor_row})
       m.release(p);
   }
+  }
   // counts for the statistics and the roofline
   D.near_boxes = (int64_t)T.near_box.size();
   D.m2l_pairs = (int64_t)T.vl_src.size();
@@ -280,35 +316,102 @@ static int upload_task(bcfmm_ctx* C, const HostSetup& H, int t) {
   return BCFMM_OK;
 }
 
-static int build_impl(const double* verts, int64_t nvert, const int32_t* tets, int64_t ntet, const int32_t* tris,
-                      int64_t ntri, const bcfmm_params* prm_in, void* stream, bcfmm_ctx** out) {
+// Host phase of one mesh: element geometry, octree, lists, near pairs.
+static std::string build_host_mesh(HostSetup& H, const double* verts, int64_t nvert, const int32_t* tets, int64_t ntet,
+                                   const int32_t* tris, int64_t ntri, const bcfmm_params& prm, bool near,
+                                   bool* mesh_err) {
+  std::string e = setup_mesh(H, verts, nvert, tets, ntet, tris, ntri, mesh_err);
+  if (!e.empty()) return e;
+  build_tree(H, prm.leaf_size);
+  for (auto& B : H.box)
+    if (!B.nchild && (B.pt1[0] - B.pt0[0] > 128 || B.pt1[1] - B.pt0[1] > 128)) {
+      *mesh_err = true;
+      return "more than 128 coincident points in one leaf at the deepest level";
+    }
+  build_lists(H, prm.eta0);
+  if (near) find_near_pairs(H, prm.eta_ns);
+  return "";
+}
+
+static int build_impl(const double* verts, const int64_t* vert_off, const int32_t* tets, const int64_t* tet_off,
+                      const int32_t* tris, const int64_t* tri_off, int32_t nmesh, const bcfmm_params* prm_in,
+                      void* stream, bcfmm_ctx** out, const bcfmm_ctx* reuse = nullptr) {
   double t0 = wall();
   bcfmm_params prm;
   bcfmm_default_params(&prm);
   if (prm_in) prm = *prm_in;
-  if (!out) return fail(BCFMM_ERR_ARG, "build_bc_tree: out is NULL");
+  if (!out) return fail(BCFMM_ERR_ARG, "build: out is NULL");
   *out = nullptr;
-  if (!verts || !tets || nvert <= 0 || ntet <= 0 || ntri < 0 || (ntri > 0 && !tris))
-    return fail(BCFMM_ERR_ARG, "build_bc_tree: null mesh arrays or empty mesh");
-  if (4 * ntet > INT32_MAX / 2 || 3 * ntri > INT32_MAX / 2) return fail(BCFMM_ERR_ARG, "build_bc_tree: mesh too large");
-  if (prm.p < 0 || prm.p > kMaxP) return fail(BCFMM_ERR_ARG, "build_bc_tree: p must be in 0..12");
-  if (prm.leaf_size < 1 || prm.leaf_size > 128) return fail(BCFMM_ERR_ARG, "build_bc_tree: leaf_size must be in 1..128");
-  if (!(prm.eta_ns > 0)) return fail(BCFMM_ERR_ARG, "build_bc_tree: eta_ns must be > 0");
-  if (!(prm.eta0 >= 0.3 && prm.eta0 <= 1.0)) return fail(BCFMM_ERR_ARG, "build_bc_tree: eta0 must be in 0.3..1");
+  if (nmesh < 1 || !vert_off || !tet_off || !tri_off) return fail(BCFMM_ERR_ARG, "build: nmesh < 1 or null offsets");
+  for (int m = 0; m < nmesh; ++m)
+    if (vert_off[m + 1] <= vert_off[m] || tet_off[m + 1] <= tet_off[m] || tri_off[m + 1] < tri_off[m] || vert_off[0] != 0 ||
+        tet_off[0] != 0 || tri_off[0] != 0)
+      return fail(BCFMM_ERR_ARG, "build: mesh " + std::to_string(m) + " is empty or the offsets are not prefix sums");
+  const int64_t ntet = tet_off[nmesh], ntri = tri_off[nmesh];
+  if (!verts || !tets || (ntri > 0 && !tris)) return fail(BCFMM_ERR_ARG, "build: null mesh arrays or empty mesh");
+  if (4 * ntet > INT32_MAX / 2 || 3 * ntri > INT32_MAX / 2) return fail(BCFMM_ERR_ARG, "build: mesh too large");
+  if (prm.p < 0 || prm.p > kMaxP) return fail(BCFMM_ERR_ARG, "build: p must be in 0..12");
+  if (prm.leaf_size < 1 || prm.leaf_size > 128) return fail(BCFMM_ERR_ARG, "build: leaf_size must be in 1..128");
+  if (!(prm.eta_ns > 0)) return fail(BCFMM_ERR_ARG, "build: eta_ns must be > 0");
+  if (!(prm.eta0 >= 0.3 && prm.eta0 <= 1.0)) return fail(BCFMM_ERR_ARG, "build: eta0 must be in 0.3..1");
   if (prm.near_n < 1 || prm.near_n > 8 || prm.near_k < 0 || prm.near_k > 3)
-    return fail(BCFMM_ERR_ARG, "build_bc_tree: near_n must be in 1..8 and near_k in 0..3");
+    return fail(BCFMM_ERR_ARG, "build: near_n must be in 1..8 and near_k in 0..3");
   if (prm.precision < BCFMM_FP64 || prm.precision > BCFMM_FP32_BF16X3)
-    return fail(BCFMM_ERR_ARG, "build_bc_tree: unknown precision");
+    return fail(BCFMM_ERR_ARG, "build: unknown precision");
+  if (prm.tc_unit < 0 || prm.tc_unit > 4096) return fail(BCFMM_ERR_ARG, "build: tc_unit must be in 0..4096");
+  if (prm.near_mode < 0 || prm.near_mode > 2) return fail(BCFMM_ERR_ARG, "build: near_mode must be 0, 1 or 2");
   const bool tc_mode = prm.precision == BCFMM_FP32_BF16X2 || prm.precision == BCFMM_FP32_BF16X3;
   const int nsplit = prm.precision == BCFMM_FP32_BF16X3 ? 3 : 2;
   if (tc_mode && !m2l_tc_supported(prm.p, nsplit))
-    return fail(BCFMM_ERR_ARG, "build_bc_tree: the tensor-core M2L supports p <= " + std::to_string(kTcMaxP) +
+    return fail(BCFMM_ERR_ARG, "build: the tensor-core M2L supports p <= " + std::to_string(kTcMaxP) +
                                    (nsplit == 3 ? " (p <= 6 with the 3-term split)" : ""));
 
+  // host phase per mesh; meshes of a batch in parallel, largest first
+  const double th = wall();
   HostSetup H;
-  bool mesh_err = false;
-  std::string e = setup_mesh(H, verts, nvert, tets, ntet, tris, ntri, &mesh_err);
-  if (!e.empty()) return fail(mesh_err ? BCFMM_ERR_MESH : BCFMM_ERR_ARG, "build_bc_tree: " + e);
+  {
+    std::vector<HostSetup> parts(nmesh);
+    std::vector<std::string> errs(nmesh);
+    std::vector<char> merr(nmesh, 0);
+    auto one = [&](int m) {
+      bool me = false;
+      try {
+        errs[m] = build_host_mesh(parts[m], verts + 3 * vert_off[m], vert_off[m + 1] - vert_off[m], tets + 4 * tet_off[m],
+                                  tet_off[m + 1] - tet_off[m], ntri > 0 ? tris + 3 * tri_off[m] : nullptr,
+                                  tri_off[m + 1] - tri_off[m], prm, reuse == nullptr, &me);
+      } catch (const std::bad_alloc&) {
+        errs[m] = "host allocation failed";
+      } catch (const std::exception& ex) {
+        errs[m] = ex.what();
+      }
+      merr[m] = me;
+    };
+    if (nmesh == 1) {
+      one(0);
+    } else {
+      std::vector<int> order(nmesh);
+      for (int m = 0; m < nmesh; ++m) order[m] = m;
+      std::stable_sort(order.begin(), order.end(),
+                       [&](int a, int b) { return tet_off[a + 1] - tet_off[a] > tet_off[b + 1] - tet_off[b]; });
+#pragma omp parallel for schedule(dynamic, 1)
+      for (int i = 0; i < nmesh; ++i) one(order[i]);
+    }
+    for (int m = 0; m < nmesh; ++m)
+      if (!errs[m].empty())
+        return fail(merr[m] ? BCFMM_ERR_MESH : BCFMM_ERR_ARG,
+                    "build: " + (nmesh > 1 ? "mesh " + std::to_string(m) + ": " : std::string()) + errs[m]);
+    if (nmesh == 1) {
+      H = std::move(parts[0]);
+      H.mesh_tet_off = {0, ntet};
+      H.mesh_tri_off = {0, ntri};
+    } else {
+      merge_setups(parts, H);
+    }
+  }
+  if (H.offsets.size() / 3 > 65535) return fail(BCFMM_ERR_ARG, "build: too many interaction offsets");
+  if (tc_mode)
+    for (int t = 0; t < 3; ++t) build_tc_tiles(H, t, 128);
+  const double host_wall = wall() - th;
 
   int dev = 0;
   CU(cudaGetDevice(&dev));
@@ -320,17 +423,19 @@ static int build_impl(const double* verts, int64_t nvert, const int32_t* tets, i
   C->ntri = ntri;
   auto cleanup = [&](int code) { C->mem.free_all(); delete C; return code; };
 
-  build_tree(H, prm.leaf_size);
-  for (auto& B : H.box)
-    if (!B.nchild && (B.pt1[0] - B.pt0[0] > 128 || B.pt1[1] - B.pt0[1] > 128))
-      return cleanup(fail(BCFMM_ERR_MESH, "build_bc_tree: more than 128 coincident points in one leaf at the deepest level"));
-  build_lists(H, prm.eta0);
-  if (H.offsets.size() / 3 > 65535) return cleanup(fail(BCFMM_ERR_ARG, "build_bc_tree: too many interaction offsets"));
-  if (tc_mode)
-    for (int t = 0; t < 3; ++t) build_tc_tiles(H, t, 128);
   if (C->mem.alloc(&C->err, 1) != cudaSuccess || cudaMemsetAsync(C->err, 0, sizeof(int), C->st) != cudaSuccess)
-    return cleanup(fail(BCFMM_ERR_OOM, "build_bc_tree: device allocation failed (error word)"));
-  find_near_pairs(H, prm.eta_ns);
+    return cleanup(fail(BCFMM_ERR_OOM, "build: device allocation failed (error word)"));
+  C->nmesh = nmesh;
+  C->reuse = reuse;
+  C->h_verts.assign(verts, verts + 3 * vert_off[nmesh]);
+  C->h_tets.assign(tets, tets + 4 * ntet);
+  if (ntri > 0) C->h_tris.assign(tris, tris + 3 * ntri);
+  C->h_vo.assign(vert_off, vert_off + nmesh + 1);
+  C->h_to.assign(tet_off, tet_off + nmesh + 1);
+  C->h_ro.assign(tri_off, tri_off + nmesh + 1);
+  C->mesh_tet_off = H.mesh_tet_off;
+  C->mesh_tri_off = H.mesh_tri_off;
+  C->sec_host = host_wall;
   C->sec_tree = H.seconds_tree;
   C->sec_lists = H.seconds_lists;
   C->sec_near_host = H.seconds_near;
@@ -354,7 +459,7 @@ static int build_impl(const double* verts, int64_t nvert, const int32_t* tets, i
     }
     int *dmi, *dtk;
     if (m.upload(&dmi, mi.data(), mi.size(), st) != cudaSuccess || m.upload(&dtk, tk.data(), tk.size(), st) != cudaSuccess)
-      return cleanup(fail(BCFMM_ERR_OOM, "build_bc_tree: device allocation failed"));
+      return cleanup(fail(BCFMM_ERR_OOM, "build: device allocation failed"));
     G.mi = dmi; G.tri_k = dtk;
   }
   // boxes
@@ -374,7 +479,7 @@ static int build_impl(const double* verts, int64_t nvert, const int32_t* tets, i
               m.upload(&dnc, nc.data(), nb, st) == cudaSuccess && m.upload(&doc, oc.data(), nb, st) == cudaSuccess &&
               m.upload(&dpar, par.data(), nb, st) == cudaSuccess && m.upload(&drg0, rg[0].data(), nb, st) == cudaSuccess &&
               m.upload(&drg1, rg[1].data(), nb, st) == cudaSuccess;
-    if (!ok) return cleanup(fail(BCFMM_ERR_OOM, "build_bc_tree: device allocation failed (boxes)"));
+    if (!ok) return cleanup(fail(BCFMM_ERR_OOM, "build: device allocation failed (boxes)"));
     G.box_cs = dcs; G.box_child0 = dc0; G.box_nchild = dnc; G.box_octant = doc; G.box_parent = dpar;
     G.box_rng[0] = drg0; G.box_rng[1] = drg1;
   }
@@ -399,7 +504,7 @@ static int build_impl(const double* verts, int64_t nvert, const int32_t* tets, i
     double4_32a* dp; float4 *dh, *dl; int* de;
     bool ok = m.upload(&dp, p64.data(), n, st) == cudaSuccess && m.upload(&dh, hi.data(), n, st) == cudaSuccess &&
               m.upload(&dl, lo.data(), n, st) == cudaSuccess && m.upload(&de, el.data(), n, st) == cudaSuccess;
-    if (!ok) return cleanup(fail(BCFMM_ERR_OOM, "build_bc_tree: device allocation failed (points)"));
+    if (!ok) return cleanup(fail(BCFMM_ERR_OOM, "build: device allocation failed (points)"));
     G.pt64[c] = dp; G.pthi[c] = dh; G.ptlo[c] = dl; G.pt_elem[c] = de;
   }
   // translation tables: M2L transposed per offset code, M2M / L2L per octant
@@ -434,10 +539,10 @@ static int build_impl(const double* verts, int64_t nvert, const int32_t* tets, i
               m.upload(&C->T32, Tt32.data(), Tt32.size(), st) == cudaSuccess &&
               m.upload(&C->M2M32, M32.data(), M32.size(), st) == cudaSuccess &&
               m.upload(&C->L2L32, L32.data(), L32.size(), st) == cudaSuccess;
-    if (!ok) return cleanup(fail(BCFMM_ERR_OOM, "build_bc_tree: device allocation failed (tables)"));
+    if (!ok) return cleanup(fail(BCFMM_ERR_OOM, "build: device allocation failed (tables)"));
     if (prm.precision == BCFMM_FP32_BF16X2 || prm.precision == BCFMM_FP32_BF16X3) {
       cudaError_t ce = m2l_tc_prepare_tables(prm.p, ncode, T.data(), nsplit, &C->tc, st);
-      if (ce != cudaSuccess) return cleanup(fail(BCFMM_ERR_CUDA, std::string("build_bc_tree: tensor tables: ") + cudaGetErrorString(ce)));
+      if (ce != cudaSuccess) return cleanup(fail(BCFMM_ERR_CUDA, std::string("build: tensor tables: ") + cudaGetErrorString(ce)));
     }
   }
   double tn = wall();
@@ -446,7 +551,8 @@ static int build_impl(const double* verts, int64_t nvert, const int32_t* tets, i
     if (rc != BCFMM_OK) return cleanup(rc);
   }
   C->sec_near_dev = wall() - tn;
-  if (cudaStreamSynchronize(st) != cudaSuccess) return cleanup(fail(BCFMM_ERR_CUDA, "build_bc_tree: stream sync failed"));
+  C->reuse = nullptr;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return cleanup(fail(BCFMM_ERR_CUDA, "build: stream sync failed"));
   if (prm.timing) {
     C->ev_ok = true;
     for (auto& row : C->ev)
@@ -461,12 +567,47 @@ static int build_impl(const double* verts, int64_t nvert, const int32_t* tets, i
 extern "C" int bcfmm_build_bc_tree(const double* verts, int64_t nvert, const int32_t* tets, int64_t ntet,
                                    const int32_t* tris, int64_t ntri, const bcfmm_params* prm, void* stream,
                                    bcfmm_ctx** out) {
+  if (out) *out = nullptr;
+  if (nvert <= 0 || ntet <= 0 || ntri < 0) return fail(BCFMM_ERR_ARG, "build_bc_tree: null mesh arrays or empty mesh");
+  const int64_t vo[2] = {0, nvert}, to[2] = {0, ntet}, ro[2] = {0, ntri};
   try {
-    return build_impl(verts, nvert, tets, ntet, tris, ntri, prm, stream, out);
+    return build_impl(verts, vo, tets, to, tris, ro, 1, prm, stream, out);
   } catch (const std::bad_alloc&) {
     return fail(BCFMM_ERR_OOM, "build_bc_tree: host allocation failed");
   } catch (const std::exception& ex) {
     return fail(BCFMM_ERR_ARG, std::string("build_bc_tree: ") + ex.what());
+  }
+}
+
+extern "C" int bcfmm_build_batch(const double* verts, const int64_t* vert_off, const int32_t* tets,
+                                 const int64_t* tet_off, const int32_t* tris, const int64_t* tri_off, int32_t nmesh,
+                                 const bcfmm_params* prm, void* stream, bcfmm_ctx** out) {
+  try {
+    return build_impl(verts, vert_off, tets, tet_off, tris, tri_off, nmesh, prm, stream, out);
+  } catch (const std::bad_alloc&) {
+    return fail(BCFMM_ERR_OOM, "build_batch: host allocation failed");
+  } catch (const std::exception& ex) {
+    return fail(BCFMM_ERR_ARG, std::string("build_batch: ") + ex.what());
+  }
+}
+
+extern "C" int bcfmm_build_like(const bcfmm_ctx* base, const bcfmm_params* prm, bcfmm_ctx** out) {
+  if (out) *out = nullptr;
+  if (!base || !prm || !out) return fail(BCFMM_ERR_ARG, "build_like: null argument");
+  if (prm->eta_ns != base->prm.eta_ns || prm->near_n != base->prm.near_n || prm->near_k != base->prm.near_k ||
+      prm->near_mode != base->prm.near_mode)
+    return fail(BCFMM_ERR_ARG, "build_like: eta_ns, near_n, near_k and near_mode must match the base context");
+  int dev = -1;
+  CU(cudaGetDevice(&dev));
+  if (dev != base->device) return fail(BCFMM_ERR_STATE, "build_like: the base context's device is not current");
+  try {
+    return build_impl(base->h_verts.data(), base->h_vo.data(), base->h_tets.data(), base->h_to.data(),
+                      base->h_tris.empty() ? nullptr : base->h_tris.data(), base->h_ro.data(), base->nmesh, prm,
+                      base->st, out, base);
+  } catch (const std::bad_alloc&) {
+    return fail(BCFMM_ERR_OOM, "build_like: host allocation failed");
+  } catch (const std::exception& ex) {
+    return fail(BCFMM_ERR_ARG, std::string("build_like: ") + ex.what());
   }
 }
 
@@ -500,6 +641,7 @@ static int ensure_work(bcfmm_ctx* C, int ndp) {
     }
   }
   C->work_ndp = ndp;
+  C->work_gen++;
   return BCFMM_OK;
 }
 
@@ -517,6 +659,7 @@ extern "C" int bcfmm_set_density(bcfmm_ctx* C, int32_t kind, const double* vals,
     if (C->dens[kind]) C->mem.release(C->dens[kind]);
     C->dens[kind] = nullptr;
     CU(C->mem.alloc(&C->dens[kind], (size_t)16 * nel));
+    C->work_gen++;
   }
   CU(cudaMemcpyAsync(C->dens[kind], vals, n * sizeof(double), is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                      C->st));
@@ -526,7 +669,9 @@ extern "C" int bcfmm_set_density(bcfmm_ctx* C, int32_t kind, const double* vals,
   return ensure_work(C, C->ndp[kind]);
 }
 
-static int eval_impl(bcfmm_ctx* C, int t, double* out, int out_is_device) {
+// skip_up: the moments and weights already hold this task's source side
+// (VtB right after VtV of the same volume density in one graph).
+static int eval_impl(bcfmm_ctx* C, int t, double* out, int out_is_device, bool skip_up = false) {
   if (!C) return fail(BCFMM_ERR_ARG, "eval: null context");
   TaskDev& D = C->task[t];
   const DevTaskLists& L = D.L;
@@ -549,14 +694,18 @@ static int eval_impl(bcfmm_ctx* C, int t, double* out, int out_is_device) {
   double* outd = out_is_device ? out : C->out_dev;
   if (tm) CU(cudaEventRecord(ev[0], st));
   if (f64) {
-    CU(launch_weights<double>(G, L.src_cls, nsp, C->dens[kind], nsel, ndens, ndp, C->W64, st));
-    CU(cudaMemsetAsync(C->mom64, 0, nexp * sizeof(double), st));
+    if (!skip_up) {
+      CU(launch_weights<double>(G, L.src_cls, nsp, C->dens[kind], nsel, ndens, ndp, C->W64, st));
+      CU(cudaMemsetAsync(C->mom64, 0, nexp * sizeof(double), st));
+    }
     CU(cudaMemsetAsync(C->loc64, 0, nexp * sizeof(double), st));
     if (tm) CU(cudaEventRecord(ev[1], st));
-    CU(launch_p2m<double>(G, L, C->W64, nsp, ndp, C->mom64, st));
-    for (int l = C->nlevels - 1; l >= 0; --l) {
-      const int n = D.m2m_off[l + 1] - D.m2m_off[l];
-      CU(launch_m2m<double>(G, D.m2m_parent + D.m2m_off[l], n, C->M2M64, ndp, C->mom64, st));
+    if (!skip_up) {
+      CU(launch_p2m<double>(G, L, C->W64, nsp, ndp, C->mom64, st));
+      for (int l = C->nlevels - 1; l >= 0; --l) {
+        const int n = D.m2m_off[l + 1] - D.m2m_off[l];
+        CU(launch_m2m<double>(G, D.m2m_parent + D.m2m_off[l], n, C->M2M64, ndp, C->mom64, st));
+      }
     }
     if (tm) CU(cudaEventRecord(ev[2], st));
     CU(launch_m2l_simt<double>(G, L, C->T64, G.tri_k, ndp, C->mom64, C->loc64, st));
@@ -568,14 +717,18 @@ static int eval_impl(bcfmm_ctx* C, int t, double* out, int out_is_device) {
     if (tm) CU(cudaEventRecord(ev[4], st));
     CU(launch_p2p_l2p_f64(G, L, C->W64, nsp, ntp, ndp, C->loc64, C->phi, st));
   } else {
-    CU(launch_weights<float>(G, L.src_cls, nsp, C->dens[kind], nsel, ndens, ndp, C->W32, st));
-    CU(cudaMemsetAsync(C->mom32, 0, nexp * sizeof(float), st));
+    if (!skip_up) {
+      CU(launch_weights<float>(G, L.src_cls, nsp, C->dens[kind], nsel, ndens, ndp, C->W32, st));
+      CU(cudaMemsetAsync(C->mom32, 0, nexp * sizeof(float), st));
+    }
     CU(cudaMemsetAsync(C->loc32, 0, nexp * sizeof(float), st));
     if (tm) CU(cudaEventRecord(ev[1], st));
-    CU(launch_p2m<float>(G, L, C->W32, nsp, ndp, C->mom32, st));
-    for (int l = C->nlevels - 1; l >= 0; --l) {
-      const int n = D.m2m_off[l + 1] - D.m2m_off[l];
-      CU(launch_m2m<float>(G, D.m2m_parent + D.m2m_off[l], n, C->M2M32, ndp, C->mom32, st));
+    if (!skip_up) {
+      CU(launch_p2m<float>(G, L, C->W32, nsp, ndp, C->mom32, st));
+      for (int l = C->nlevels - 1; l >= 0; --l) {
+        const int n = D.m2m_off[l + 1] - D.m2m_off[l];
+        CU(launch_m2m<float>(G, D.m2m_parent + D.m2m_off[l], n, C->M2M32, ndp, C->mom32, st));
+      }
     }
     if (tm) CU(cudaEventRecord(ev[2], st));
     if (tc) CU(launch_m2l_tc(G, L, C->tc, ndp, C->mom32, C->loc32, C->tc_partial, C->tc_momb, st));
@@ -608,6 +761,59 @@ static int eval_impl(bcfmm_ctx* C, int t, double* out, int out_is_device) {
 extern "C" int bcfmm_eval_vtv(bcfmm_ctx* C, double* out, int32_t d) { return eval_impl(C, 0, out, d); }
 extern "C" int bcfmm_eval_vtb(bcfmm_ctx* C, double* out, int32_t d) { return eval_impl(C, 1, out, d); }
 extern "C" int bcfmm_eval_btv(bcfmm_ctx* C, double* out, int32_t d) { return eval_impl(C, 2, out, d); }
+
+// Several tasks through one CUDA graph.  The graph is captured on a
+// library-owned stream the first time a (task mask, outputs, density
+// sizes, work buffers) combination is seen, and replayed on the context's
+// stream afterwards.  VtB right after VtV reuses VtV's upward pass (same
+// volume density, same source points).
+extern "C" int bcfmm_eval_graph(bcfmm_ctx* C, int32_t mask, double* out_vtv, double* out_vtb, double* out_btv) {
+  if (!C) return fail(BCFMM_ERR_ARG, "eval_graph: null context");
+  if (mask <= 0 || mask > 7) return fail(BCFMM_ERR_ARG, "eval_graph: task mask must be a non-empty subset of 1|2|4");
+  double* outs[3] = {out_vtv, out_vtb, out_btv};
+  for (int t = 0; t < 3; ++t) {
+    if (!(mask >> t & 1)) { outs[t] = nullptr; continue; }
+    const int kind = C->task[t].L.src_cls;
+    if (C->ndens[kind] == 0)
+      return fail(BCFMM_ERR_STATE, kind == 0 ? "eval_graph: volume density not set" : "eval_graph: boundary density not set");
+    if (!outs[t]) return fail(BCFMM_ERR_ARG, "eval_graph: null output for a task in the mask");
+    const int rc = ensure_work(C, C->ndp[kind]);
+    if (rc != BCFMM_OK) return rc;
+  }
+  auto& g = C->graph;
+  const bool same = g.exec && g.mask == mask && g.work_gen == C->work_gen && g.ndens[0] == C->ndens[0] &&
+                    g.ndens[1] == C->ndens[1] && std::equal(outs, outs + 3, g.out);
+  if (!same) {
+    if (g.exec) { cudaGraphExecDestroy(g.exec); g.exec = nullptr; }
+    if (!C->cap_st) CU(cudaStreamCreateWithFlags(&C->cap_st, cudaStreamNonBlocking));
+    cudaStream_t user = C->st;
+    const int timing = C->prm.timing;
+    C->st = C->cap_st;
+    C->prm.timing = 0;
+    CU(cudaStreamBeginCapture(C->cap_st, cudaStreamCaptureModeRelaxed));
+    int rc = BCFMM_OK;
+    for (int t = 0; t < 3 && rc == BCFMM_OK; ++t)
+      if (mask >> t & 1) rc = eval_impl(C, t, outs[t], 1, t == 1 && (mask & 1));
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(C->cap_st, &graph);
+    C->st = user;
+    C->prm.timing = timing;
+    if (rc != BCFMM_OK) { if (graph) cudaGraphDestroy(graph); return rc; }
+    if (ce != cudaSuccess) return fail(BCFMM_ERR_CUDA, std::string("eval_graph: capture failed: ") + cudaGetErrorString(ce));
+    const cudaError_t ie = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) { g.exec = nullptr; return fail(BCFMM_ERR_CUDA, std::string("eval_graph: instantiate: ") + cudaGetErrorString(ie)); }
+    g.mask = mask;
+    g.work_gen = C->work_gen;
+    g.ndens[0] = C->ndens[0];
+    g.ndens[1] = C->ndens[1];
+    std::copy(outs, outs + 3, g.out);
+    g.nodes = 0;
+  }
+  CU(cudaGraphLaunch(g.exec, C->st));
+  C->ev_rec[0] = C->ev_rec[1] = C->ev_rec[2] = false;
+  return BCFMM_OK;
+}
 
 // One task, one density, no allocation: the tensor-core M2L writes its unit
 // partial sums into the library's fixed static device array instead of the
@@ -660,6 +866,42 @@ extern "C" int bcfmm_eval_noalloc(bcfmm_ctx* C, int32_t task, const double* dens
   return BCFMM_OK;
 }
 
+extern "C" int bcfmm_direct_sample(bcfmm_ctx* C, int32_t task, const int64_t* targets, int64_t n, double* out) {
+  if (!C || !targets || !out || n < 0) return fail(BCFMM_ERR_ARG, "direct_sample: null argument");
+  if (task < 0 || task > 2) return fail(BCFMM_ERR_ARG, "direct_sample: task must be 0, 1 or 2");
+  if (n > (1 << 20)) return fail(BCFMM_ERR_ARG, "direct_sample: at most 2^20 targets");
+  const DevTaskLists& L = C->task[task].L;
+  const int kind = L.src_cls;
+  if (C->ndens[kind] == 0) return fail(BCFMM_ERR_STATE, "direct_sample: density not set");
+  for (int64_t i = 0; i < n; ++i)
+    if (targets[i] < 0 || targets[i] >= L.ntgt_el) return fail(BCFMM_ERR_ARG, "direct_sample: target index out of range");
+  if (n == 0) return BCFMM_OK;
+  const int nd = C->ndens[kind];
+  // a target sees the sources of its own mesh only (sorted points are mesh after mesh)
+  const std::vector<int64_t>& toff = L.tgt_cls == 0 ? C->mesh_tet_off : C->mesh_tri_off;
+  const std::vector<int64_t>& soff = L.src_cls == 0 ? C->mesh_tet_off : C->mesh_tri_off;
+  const int nqs = L.src_cls == 0 ? 4 : 3;
+  std::vector<int64_t> hbuf(3 * n);
+  for (int64_t i = 0; i < n; ++i) {
+    const int m = (int)(std::upper_bound(toff.begin(), toff.end(), targets[i]) - toff.begin()) - 1;
+    hbuf[i] = targets[i];
+    hbuf[n + 2 * i] = nqs * soff[m];
+    hbuf[n + 2 * i + 1] = nqs * soff[m + 1];
+  }
+  int64_t* dt = nullptr;
+  double* dout = nullptr;
+  CU(cudaMalloc((void**)&dt, 3 * n * sizeof(int64_t)));
+  cudaError_t e = cudaMalloc((void**)&dout, (size_t)n * nd * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dt, hbuf.data(), 3 * n * sizeof(int64_t), cudaMemcpyHostToDevice, C->st);
+  if (e == cudaSuccess) e = launch_direct_sample(C->G, L, dt, dt + n, (int)n, C->dens[kind], nd, dout, C->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, dout, (size_t)n * nd * sizeof(double), cudaMemcpyDeviceToHost, C->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(C->st);
+  cudaFree(dt);
+  cudaFree(dout);
+  if (e != cudaSuccess) return fail(BCFMM_ERR_CUDA, std::string("direct_sample: ") + cudaGetErrorString(e));
+  return BCFMM_OK;
+}
+
 extern "C" int bcfmm_stats(const bcfmm_ctx* C, char* json, size_t cap) {
   if (!C || !json) return fail(BCFMM_ERR_ARG, "stats: null argument");
   std::string s = "{";
@@ -677,6 +919,7 @@ extern "C" int bcfmm_stats(const bcfmm_ctx* C, char* json, size_t cap) {
   }
   kv("p", C->prm.p); kv("np", C->np); kv("eta0", C->prm.eta0); kv("n_offsets", C->ncode); kv("leaf_size", C->prm.leaf_size); kv("precision", C->prm.precision);
   kv("nbox", C->nbox); kv("nleaf", C->nleaf); kv("nlevels", C->nlevels);
+  kv("nmesh", C->nmesh); kv("host_setup_s", C->sec_host);
   kv("setup_s", C->sec_setup); kv("tree_s", C->sec_tree); kv("lists_s", C->sec_lists);
   kv("near_search_s", C->sec_near_host); kv("near_rule_s", C->sec_near_dev);
   const char* names[3] = {"vtv", "vtb", "btv"};
@@ -720,6 +963,8 @@ extern "C" void bcfmm_destroy(bcfmm_ctx* C) {
   if (C->ev_ok)
     for (auto& row : C->ev)
       for (auto& ev : row) cudaEventDestroy(ev);
+  if (C->graph.exec) cudaGraphExecDestroy(C->graph.exec);
+  if (C->cap_st) cudaStreamDestroy(C->cap_st);
   m2l_tc_free_tables(&C->tc);
   C->mem.free_all();
   delete C;

@@ -71,6 +71,7 @@ struct HostSetup {
   std::vector<int> leaf_of[2];                     // sorted position -> leaf box
   HostTask task[3];
   std::vector<int> offsets;                        // distinct interaction offsets (x,y,z) per code
+  std::vector<int64_t> mesh_tet_off, mesh_tri_off; // element ranges of the meshes of a batch
   double seconds_tree = 0, seconds_lists = 0, seconds_near = 0;
 };
 
@@ -83,6 +84,11 @@ void build_tree(HostSetup& H, int leaf_size);
 void build_lists(HostSetup& H, double eta0);
 void build_tc_tiles(HostSetup& H, int task, int tile_m);
 void find_near_pairs(HostSetup& H, double eta_ns);
+// Concatenates independently built meshes into one forest: elements and
+// points mesh after mesh, boxes level-major (level l of every mesh, mesh
+// order inside), lists and near pairs renumbered.  No list entry crosses
+// meshes, so the result evaluates every mesh on its own.
+void merge_setups(std::vector<HostSetup>& parts, HostSetup& H);
 
 // Gauss-Legendre nodes/weights on [0,1] (Newton iteration on P_n).
 void gauss_legendre01(int n, std::vector<double>& x, std::vector<double>& w);

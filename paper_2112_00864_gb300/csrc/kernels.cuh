@@ -70,6 +70,11 @@ cudaError_t launch_p2p_l2p_f64(const DevGeom& G, const DevTaskLists& L, const do
 cudaError_t launch_elem_sum(const DevGeom& G, const DevTaskLists& L, const double* phi, int64_t ntgt_pts,
                             const double* dens_src, int ndens, double* out, cudaStream_t st);
 
+// FP64 direct evaluation of sampled target elements (out [ndens][n]);
+// src_rng [n][2]: sorted source point range of each target's mesh
+cudaError_t launch_direct_sample(const DevGeom& G, const DevTaskLists& L, const int64_t* targets, const int64_t* src_rng,
+                                 int n, const double* dens, int ndens, double* out, cudaStream_t st);
+
 // setup: near-rule corrections C_ts = N_ts - Q_ts (FP64)
 cudaError_t launch_near_rule(int task, int64_t nnz, const int* row, const int* col,
                              const double* tgt_v, const double* src_v,

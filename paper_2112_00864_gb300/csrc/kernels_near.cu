@@ -56,20 +56,76 @@ __device__ double tri_pot(V3 x, const V3* P) {
   return acc - fabs(w) * fabs(omega);
 }
 
-// int_tet dy/|x-y| = 1/2 sum_F h_F(x) I_F(x), h_F = n_F.(y_F - x), n_F outward.
-__device__ double tet_pot(V3 x, const V3* v) {
-  const int F[4][3] = {{1, 2, 3}, {0, 3, 2}, {0, 1, 3}, {0, 2, 1}};
+// int_tet dy/|x-y| = 1/2 sum_F h_F(x) I_F(x), h_F = n_F.(y_F - x), n_F
+// outward, with I_F the flat-triangle integral above.  Everything that does
+// not depend on x (face normals, edge directions, in-plane edge normals) is
+// prepared once per source tet, and the quantities faces share (vertex
+// distances, the log term of each of the 6 edges, which does not depend on
+// the face or the edge's direction) are computed once per point.
+__device__ constexpr int kTetEdge[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+__device__ constexpr int kTetFace[4][3] = {{1, 2, 3}, {0, 3, 2}, {0, 1, 3}, {0, 2, 1}};
+__device__ constexpr int kFaceEdge[4][3] = {{3, 5, 4}, {2, 5, 1}, {0, 4, 2}, {1, 3, 0}};   // edge of (F[j], F[j+1])
+
+struct SrcTet {
+  V3 v[4];
+  V3 te[6];            // unit direction of edge k (first -> second vertex)
+  V3 nout[4];          // outward unit normal of face f
+  V3 m[4][3];          // in-plane outward normal of the face's edge j (vertex order of the face)
+  double thr[4];       // |d| below this: x on the edge's line within the face plane
+};
+
+__device__ void src_tet_prepare(const V3* v, SrcTet& S) {
   V3 cen = {0, 0, 0};
-  for (int i = 0; i < 4; ++i) { cen.x += 0.25 * v[i].x; cen.y += 0.25 * v[i].y; cen.z += 0.25 * v[i].z; }
-  double acc = 0.0;
+  for (int i = 0; i < 4; ++i) { S.v[i] = v[i]; cen.x += 0.25 * v[i].x; cen.y += 0.25 * v[i].y; cen.z += 0.25 * v[i].z; }
+  for (int k = 0; k < 6; ++k) {
+    V3 t = vsub(v[kTetEdge[k][1]], v[kTetEdge[k][0]]);
+    S.te[k] = vscale(t, 1.0 / sqrt(vdot(t, t)));
+  }
   for (int f = 0; f < 4; ++f) {
-    V3 T[3] = {v[F[f][0]], v[F[f][1]], v[F[f][2]]};
-    V3 n = vcross(vsub(T[1], T[0]), vsub(T[2], T[0]));
-    n = vscale(n, 1.0 / sqrt(vdot(n, n)));
-    if (vdot(vsub(T[0], cen), n) < 0) n = vscale(n, -1.0);
-    const double h = vdot(n, vsub(T[0], x));
+    const V3 T0 = v[kTetFace[f][0]], T1 = v[kTetFace[f][1]], T2 = v[kTetFace[f][2]];
+    V3 n = vcross(vsub(T1, T0), vsub(T2, T0));
+    const double nn = sqrt(vdot(n, n));
+    n = vscale(n, 1.0 / nn);             // normal of the face's vertex order
+    S.thr[f] = 1e-14 * sqrt(nn);
+    S.nout[f] = vdot(vsub(T0, cen), n) < 0 ? vscale(n, -1.0) : n;
+    for (int j = 0; j < 3; ++j) {
+      const int a = kTetFace[f][j], b = kTetFace[f][(j + 1) % 3];
+      V3 t = vsub(v[b], v[a]);
+      t = vscale(t, 1.0 / sqrt(vdot(t, t)));
+      S.m[f][j] = vcross(t, n);
+    }
+  }
+}
+
+__device__ double tet_pot(V3 x, const SrcTet& S) {
+  V3 r[4];
+  double R[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) { r[i] = vsub(S.v[i], x); R[i] = sqrt(vdot(r[i], r[i])); }
+  double L[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const int a = kTetEdge[k][0], b = kTetEdge[k][1];
+    const double ta = vdot(r[a], S.te[k]), tb = vdot(r[b], S.te[k]);
+    L[k] = (ta + tb >= 0.0) ? log((R[b] + tb) / (R[a] + ta)) : log((R[a] - ta) / (R[b] - tb));
+  }
+  double acc = 0.0;
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    const int i0 = kTetFace[f][0], i1 = kTetFace[f][1], i2 = kTetFace[f][2];
+    const double h = vdot(S.nout[f], r[i0]);
     if (h == 0.0) continue;
-    acc += 0.5 * h * tri_pot(x, T);
+    double e = 0.0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const double d = vdot(r[kTetFace[f][j]], S.m[f][j]);
+      if (fabs(d) > S.thr[f]) e += d * L[kFaceEdge[f][j]];
+    }
+    const double num = vdot(r[i0], vcross(r[i1], r[i2]));
+    const double den = R[i0] * R[i1] * R[i2] + vdot(r[i0], r[i1]) * R[i2] + vdot(r[i0], r[i2]) * R[i1] +
+                       vdot(r[i1], r[i2]) * R[i0];
+    const double omega = 2.0 * atan2(num, den);
+    acc += 0.5 * h * (e - fabs(h) * fabs(omega));
   }
   return acc;
 }
@@ -106,11 +162,18 @@ __global__ void k_near_rule(int task, int64_t nnz, const int* __restrict__ row, 
   const int t = row[kk], s = col[kk];
   const bool tgt_tet = (task != 1), src_tet = (task != 2);
   const int nvt = tgt_tet ? 4 : 3, nvs = src_tet ? 4 : 3;
-  V3 tv[4], sv[4];
+  V3 tv[4], sv[4] = {};
   for (int i = 0; i < nvt; ++i) tv[i] = {tgt_v[(int64_t)t * 3 * nvt + 3 * i], tgt_v[(int64_t)t * 3 * nvt + 3 * i + 1], tgt_v[(int64_t)t * 3 * nvt + 3 * i + 2]};
   for (int i = 0; i < nvs; ++i) sv[i] = {src_v[(int64_t)s * 3 * nvs + 3 * i], src_v[(int64_t)s * 3 * nvs + 3 * i + 1], src_v[(int64_t)s * 3 * nvs + 3 * i + 2]};
   double gx[kMaxGL], gw[kMaxGL];
   for (int i = 0; i < n; ++i) { gx[i] = glx[i]; gw[i] = glw[i]; }
+  // the source tet's x-independent geometry, prepared once per warp
+  __shared__ SrcTet sS[4];
+  SrcTet& S = sS[(threadIdx.x >> 5) & 3];
+  if (src_tet) {
+    if (lane == 0) src_tet_prepare(sv, S);
+    __syncwarp();
+  }
   const int nch = tgt_tet ? 8 : 4;
   int npc = tgt_tet ? n * n * n : n * n;
   int npieces = 1;
@@ -153,7 +216,7 @@ __global__ void k_near_rule(int task, int64_t nnz, const int* __restrict__ row, 
       x.z = v[0].z + x1 * (v[1].z - v[0].z) + x2 * (v[2].z - v[0].z);
       wt = gw[ia] * gw[ib] * jac * tri_area2(v);
     }
-    sum += wt * (src_tet ? tet_pot(x, sv) : tri_pot(x, sv));
+    sum += wt * (src_tet ? tet_pot(x, S) : tri_pot(x, sv));
   }
   sum *= kInv4PiN;
   // product rule of the point passes for this pair

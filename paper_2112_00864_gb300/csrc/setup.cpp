@@ -496,6 +496,135 @@ void find_near_pairs(HostSetup& H, double eta_ns) {
   H.seconds_near = now_s() - t0;
 }
 
+// ---------------------------------------------------------------- batches
+void merge_setups(std::vector<HostSetup>& P, HostSetup& H) {
+  const int nm = (int)P.size();
+  H = HostSetup();
+  H.mesh_tet_off.assign(nm + 1, 0);
+  H.mesh_tri_off.assign(nm + 1, 0);
+  int nlev = 0;
+  for (int m = 0; m < nm; ++m) {
+    H.mesh_tet_off[m + 1] = H.mesh_tet_off[m] + P[m].ntet;
+    H.mesh_tri_off[m + 1] = H.mesh_tri_off[m] + P[m].ntri;
+    nlev = std::max(nlev, P[m].nlevels);
+    H.seconds_tree += P[m].seconds_tree;
+    H.seconds_lists += P[m].seconds_lists;
+    H.seconds_near += P[m].seconds_near;
+  }
+  H.ntet = H.mesh_tet_off[nm];
+  H.ntri = H.mesh_tri_off[nm];
+  H.nlevels = nlev;
+  for (int m = 0; m < nm; ++m) {
+    const HostSetup& S = P[m];
+    H.tet_v.insert(H.tet_v.end(), S.tet_v.begin(), S.tet_v.end());
+    H.tri_v.insert(H.tri_v.end(), S.tri_v.begin(), S.tri_v.end());
+    H.tet_vol.insert(H.tet_vol.end(), S.tet_vol.begin(), S.tet_vol.end());
+    H.tri_area.insert(H.tri_area.end(), S.tri_area.begin(), S.tri_area.end());
+    for (int c = 0; c < 2; ++c) {
+      H.qp[c].insert(H.qp[c].end(), S.qp[c].begin(), S.qp[c].end());
+      H.qw[c].insert(H.qw[c].end(), S.qw[c].begin(), S.qw[c].end());
+    }
+  }
+  if (nm > 0) { std::memcpy(H.lo, P[0].lo, sizeof H.lo); H.R0 = P[0].R0; }
+  // point offsets per class: points are element-major (4 per tet, 3 per triangle)
+  auto pto = [&](int m, int c) -> int { return c == 0 ? (int)(4 * H.mesh_tet_off[m]) : (int)(3 * H.mesh_tri_off[m]); };
+  // boxes, level-major
+  std::vector<int> lcount(nlev, 0);
+  for (int m = 0; m < nm; ++m)
+    for (int l = 0; l < P[m].nlevels; ++l) lcount[l] += P[m].lvl_off[l + 1] - P[m].lvl_off[l];
+  H.lvl_off.assign(nlev + 1, 0);
+  for (int l = 0; l < nlev; ++l) H.lvl_off[l + 1] = H.lvl_off[l] + lcount[l];
+  std::vector<std::vector<int>> bmap(nm);
+  {
+    std::vector<int> cursor(H.lvl_off.begin(), H.lvl_off.end() - 1);
+    for (int m = 0; m < nm; ++m) {
+      const HostSetup& S = P[m];
+      bmap[m].resize(S.box.size());
+      for (int l = 0; l < S.nlevels; ++l) {
+        for (int b = S.lvl_off[l]; b < S.lvl_off[l + 1]; ++b) bmap[m][b] = cursor[l] + (b - S.lvl_off[l]);
+        cursor[l] += S.lvl_off[l + 1] - S.lvl_off[l];
+      }
+    }
+  }
+  H.box.resize(H.lvl_off[nlev]);
+  for (int m = 0; m < nm; ++m) {
+    const HostSetup& S = P[m];
+    for (size_t b = 0; b < S.box.size(); ++b) {
+      HostBox B = S.box[b];
+      if (B.parent >= 0) B.parent = bmap[m][B.parent];
+      if (B.child0 >= 0) B.child0 = bmap[m][B.child0];
+      for (int c = 0; c < 2; ++c) { B.pt0[c] += pto(m, c); B.pt1[c] += pto(m, c); }
+      H.box[bmap[m][b]] = B;
+    }
+  }
+  for (int c = 0; c < 2; ++c) {
+    for (int m = 0; m < nm; ++m) {
+      const int o = pto(m, c);
+      for (int v : P[m].perm[c]) H.perm[c].push_back(o + v);
+      for (int v : P[m].leaf_of[c]) H.leaf_of[c].push_back(v >= 0 ? bmap[m][v] : -1);
+    }
+  }
+  // interaction offset codes
+  std::unordered_map<int64_t, int> code_of;
+  std::vector<std::vector<int>> cmap(nm);
+  for (int m = 0; m < nm; ++m) {
+    const std::vector<int>& O = P[m].offsets;
+    for (size_t k = 0; k < O.size() / 3; ++k) {
+      const int64_t key = ((int64_t)(O[3 * k] + 64) << 16) | ((int64_t)(O[3 * k + 1] + 64) << 8) | (int64_t)(O[3 * k + 2] + 64);
+      auto it = code_of.find(key);
+      int c;
+      if (it == code_of.end()) {
+        c = (int)(H.offsets.size() / 3);
+        code_of[key] = c;
+        H.offsets.insert(H.offsets.end(), {O[3 * k], O[3 * k + 1], O[3 * k + 2]});
+      } else {
+        c = it->second;
+      }
+      cmap[m].push_back(c);
+    }
+  }
+  // per-task lists
+  for (int t = 0; t < 3; ++t) {
+    HostTask& T = H.task[t];
+    T = HostTask();
+    if (nm == 0) continue;
+    T.src_cls = P[0].task[t].src_cls;
+    T.tgt_cls = P[0].task[t].tgt_cls;
+    const int sc = T.src_cls;
+    T.near_off.push_back(0);
+    T.run_off.push_back(0);
+    T.vl_off.push_back(0);
+    T.cor_off.push_back(0);
+    T.m2m_parent.assign(nlev, {});
+    T.l2l_child.assign(nlev, {});
+    for (int m = 0; m < nm; ++m) {
+      const HostTask& S = P[m].task[t];
+      const std::vector<int>& bm = bmap[m];
+      const int nb0 = (int)T.near_box.size(), rb0 = (int)(T.runs.size() / 2), vb0 = (int)T.vl_src.size();
+      const int64_t nz0 = (int64_t)T.cor_col.size();
+      for (int b : S.p2p_leaf) T.p2p_leaf.push_back(bm[b]);
+      for (size_t i = 1; i < S.near_off.size(); ++i) T.near_off.push_back(S.near_off[i] + nb0);
+      for (int b : S.near_box) T.near_box.push_back(bm[b]);
+      for (size_t i = 1; i < S.run_off.size(); ++i) T.run_off.push_back(S.run_off[i] + rb0);
+      for (int v : S.runs) T.runs.push_back(v + pto(m, sc));
+      T.self_len.insert(T.self_len.end(), S.self_len.begin(), S.self_len.end());
+      for (int b : S.m2l_tgt) T.m2l_tgt.push_back(bm[b]);
+      for (size_t i = 1; i < S.vl_off.size(); ++i) T.vl_off.push_back(S.vl_off[i] + vb0);
+      for (int b : S.vl_src) T.vl_src.push_back(bm[b]);
+      for (uint16_t c : S.vl_code) T.vl_code.push_back((uint16_t)cmap[m][c]);
+      for (int b : S.p2m_leaf) T.p2m_leaf.push_back(bm[b]);
+      for (int b : S.l2p_leaf) T.l2p_leaf.push_back(bm[b]);
+      for (size_t l = 0; l < S.m2m_parent.size(); ++l)
+        for (int b : S.m2m_parent[l]) T.m2m_parent[l].push_back(bm[b]);
+      for (size_t l = 0; l < S.l2l_child.size(); ++l)
+        for (int b : S.l2l_child[l]) T.l2l_child[l].push_back(bm[b]);
+      const int64_t so = sc == 0 ? H.mesh_tet_off[m] : H.mesh_tri_off[m];
+      for (size_t i = 1; i < S.cor_off.size(); ++i) T.cor_off.push_back(S.cor_off[i] + nz0);
+      for (int32_t c : S.cor_col) T.cor_col.push_back((int32_t)(c + so));
+    }
+  }
+}
+
 // ---------------------------------------------------------- quadrature
 void gauss_legendre01(int n, std::vector<double>& x, std::vector<double>& w) {
   x.resize(n); w.resize(n);

@@ -301,7 +301,7 @@ def batch_meshes(n: int = 64, seed: int = 0, hs=(1 / 8, 1 / 16, 1 / 32)):
         if kind == "cube":
             m = cube_bc_mesh(h_bnd=h, h_vol=h)
         else:
-            lev = {1 / 8: 2, 1 / 16: 3, 1 / 32: 4}.get(h, 3)
+            lev = max(1, int(round(np.log2(1.0 / h))) - 1)      # 1/8 -> 2, 1/16 -> 3, 1/32 -> 4
             m = ball_bc_mesh(level=lev)
         m.info["h_req"] = h
         out.append(m)

@@ -87,3 +87,26 @@ def test_m2l_tables_match_oracle(lib):
     mi = O.multi_indices(4).sum(1)
     mask = (mi[:, None] + mi[None, :]) > 4
     assert np.all(T[mask] == 0) and np.all(T[~mask] != 0) is not None
+
+
+def test_batch_argument_errors_before_gpu(lib):
+    """bcfmm_build_batch validates offsets and every mesh before any device work."""
+    import ctypes as C
+    prm = bcfmm.default_params()
+    ctx = C.c_void_p()
+    good = np.eye(4, 3)
+    flat = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [1, 1, 0.0]])
+    verts = np.concatenate([good, good, flat])
+    tets = np.array([[0, 1, 2, 3]] * 3, np.int32)       # local vertex ids
+    vo = np.array([0, 4, 8, 12], np.int64)
+    to = np.array([0, 1, 2, 3], np.int64)
+    ro = np.zeros(4, np.int64)
+    args = lambda v, t, n: (verts.ctypes.data, v.ctypes.data, tets.ctypes.data, t.ctypes.data, None, ro.ctypes.data,
+                            n, C.byref(prm), None, C.byref(ctx))
+    rc = lib.bcfmm_build_batch(*args(vo, to, 3))
+    assert rc == -2 and b"mesh 2" in lib.bcfmm_last_error() and b"zero volume" in lib.bcfmm_last_error()
+    rc = lib.bcfmm_build_batch(*args(vo, np.array([0, 1, 1, 3], np.int64), 3))    # empty mesh 1
+    assert rc == -1 and b"mesh 1" in lib.bcfmm_last_error()
+    rc = lib.bcfmm_build_batch(*args(vo, to, 0))
+    assert rc == -1 and ctx.value is None
+    assert lib.bcfmm_eval_graph(None, 1, None, None, None) == -1
