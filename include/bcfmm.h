@@ -94,7 +94,7 @@ typedef struct {
                            2 = no correction: product rule only (the reference point
                                the learned correction is measured against)             */
   double mlp_tol;       /* near_mode 1: largest accepted calibrated error of one pair's
-                           correction, relative to the pair's product-rule value; 1e-3 */
+                           correction, relative to the pair's product-rule value; 5e-3 */
   const void* mlp_blob; /* near_mode 1: trained network and calibration, format of
                            bcfmm_mlp_blob_size(); read during the build only           */
   int64_t mlp_blob_bytes;
@@ -245,6 +245,56 @@ int bcfmm_eval_noalloc(bcfmm_ctx* ctx, int32_t task, const double* dens_dev, dou
  * not set), BCFMM_ERR_CUDA.
  */
 int bcfmm_direct_sample(bcfmm_ctx* ctx, int32_t task, const int64_t* targets, int64_t n, double* out);
+
+/*
+ * Learned correction of near-singular pairs (bcfmm_params.near_mode 1).
+ * The paper computes every near pair with an accurate rule; this optional
+ * path replaces the rule, for pairs whose closures are apart, by a small
+ * network trained on the GPU with the kernels below.
+ *
+ * Pair features (12): the source vertices in the affine frame of the target
+ * (target vertices t0..t3, frame columns t1-t0, t2-t0, t3-t0; a triangle
+ * target uses its unit normal times sqrt(2 area) on the source's side as
+ * the third column), centred at the target centroid; both vertex orders
+ * ascending in distance to the other element's centroid; a triangle
+ * source fills 9 slots, the rest 0.
+ * qhat (16): product-rule terms q_ij = W_i W_j / (4 pi r_ij) in those
+ * orders (i target point, j source point, [4][4], unused slots 0) over their
+ * sum Q.  Network 12 -> 64 -> 64 -> 16 (exact GELU), output dw; the pair's
+ * correction is Q * sum_k dw_k qhat_k.  Parameters, FP32 [6032]:
+ * W1[64][12] b1[64] W2[64][64] b2[64] W3[16][64] b3[16]; the kernels compute
+ * with their BF16 roundings and FP32 accumulation.
+ * Blob (bcfmm_mlp_blob_size() bytes): uint32 header {0x4C4D4342, 1, 6032,
+ * 32, has_vtv, has_vtb, has_btv, 0}, then per task params[6032] and the
+ * calibrated error of each of 32 geometric bins, float32.
+ * All pointers below are device memory unless stated; stream is a
+ * cudaStream_t (NULL = legacy default stream).
+ */
+int64_t bcfmm_mlp_blob_size(void);
+
+/* Training data from a context built with near_mode 1 or 2: up to max_pairs
+ * of its near-singular pairs of `task`, evenly spaced in CSR order.
+ *   feat [max][12], qhat [max][16], chat [max] FP32: label (N - Q) / Q with
+ *   N the FP64 near rule; bin [max] int32 calibration bin; pairs [max][2]
+ *   int32 (target, source) element indices; *n_out (host) pairs written.
+ * Synchronises the context's stream.
+ * Errors: BCFMM_ERR_STATE (context built with near_mode 0), BCFMM_ERR_ARG. */
+int bcfmm_mlp_dataset(bcfmm_ctx* ctx, int32_t task, int64_t max_pairs, float* feat, float* qhat, float* chat,
+                      int32_t* bin, int32_t* pairs, int64_t* n_out);
+
+/* grad[6032] and loss[1] (both zeroed first) of the mean over n pairs of
+ * (sum_k dw_k qhat_k - chat)^2, gradient with respect to the BF16-rounded
+ * parameters (applied to the FP32 masters by bcfmm_mlp_adam). */
+int bcfmm_mlp_grad(const float* params, const float* feat, const float* qhat, const float* chat, int64_t n,
+                   float* grad, float* loss, void* stream);
+
+/* One Adam step (step >= 1, bias-corrected) on the FP32 masters. */
+int bcfmm_mlp_adam(float* params, const float* grad, float* m1, float* m2, int32_t step, float lr, float beta1,
+                   float beta2, float eps, void* stream);
+
+/* out[n] = sum_k dw_k qhat_k for each pair (inference on BF16 weights). */
+int bcfmm_mlp_predict(const float* params, const float* feat, const float* qhat, int64_t n, float* out,
+                      void* stream);
 
 /*
  * Context statistics as one JSON object (points, boxes, levels, list sizes,

@@ -23,7 +23,9 @@ VOLUME, BOUNDARY = 0, 1
 EXPORTED = ["bcfmm_default_params", "bcfmm_build_bc_tree", "bcfmm_set_density", "bcfmm_eval_vtv",
             "bcfmm_eval_vtb", "bcfmm_eval_btv", "bcfmm_stats", "bcfmm_last_error", "bcfmm_destroy",
             "bcfmm_debug_m2l_matrix", "bcfmm_eval_noalloc", "bcfmm_build_batch", "bcfmm_eval_graph",
-            "bcfmm_build_like", "bcfmm_direct_sample"]
+            "bcfmm_build_like", "bcfmm_direct_sample", "bcfmm_mlp_blob_size", "bcfmm_mlp_dataset",
+            "bcfmm_mlp_grad", "bcfmm_mlp_adam", "bcfmm_mlp_predict"]
+NEAR_MODE = {"fp64": 0, "learned": 1, "none": 2}
 TASK_BIT = {"vtv": 1, "vtb": 2, "btv": 4}
 
 
@@ -78,6 +80,16 @@ def load(path: str = LIB_PATH):
         L.bcfmm_build_like.restype = C.c_int
         L.bcfmm_direct_sample.argtypes = [p, i32, p, i64, p]
         L.bcfmm_direct_sample.restype = C.c_int
+        L.bcfmm_mlp_blob_size.argtypes = []
+        L.bcfmm_mlp_blob_size.restype = C.c_int64
+        L.bcfmm_mlp_dataset.argtypes = [p, i32, i64, p, p, p, p, p, C.POINTER(C.c_int64)]
+        L.bcfmm_mlp_dataset.restype = C.c_int
+        L.bcfmm_mlp_grad.argtypes = [p, p, p, p, i64, p, p, p]
+        L.bcfmm_mlp_grad.restype = C.c_int
+        L.bcfmm_mlp_adam.argtypes = [p, p, p, p, i32, C.c_float, C.c_float, C.c_float, C.c_float, p]
+        L.bcfmm_mlp_adam.restype = C.c_int
+        L.bcfmm_mlp_predict.argtypes = [p, p, p, i64, p, p]
+        L.bcfmm_mlp_predict.restype = C.c_int
         _lib = L
     return _lib
 
@@ -87,13 +99,26 @@ def _check(rc: int):
         raise BcfmmError(rc, load().bcfmm_last_error().decode())
 
 
+def _set(prm: Params, k, v):
+    if k == "precision" and isinstance(v, str):
+        v = PRECISION[v]
+    if k == "near_mode" and isinstance(v, str):
+        v = NEAR_MODE[v]
+    if k == "mlp_blob":
+        # keep the bytes alive with the Params object; the library reads
+        # them during the build only
+        buf = C.create_string_buffer(bytes(v), len(v))
+        prm._blob = buf
+        prm.mlp_blob_bytes = len(v)
+        v = C.cast(buf, C.c_void_p)
+    setattr(prm, k, v)
+
+
 def default_params(**kw) -> Params:
     prm = Params()
     load().bcfmm_default_params(C.byref(prm))
     for k, v in kw.items():
-        if k == "precision" and isinstance(v, str):
-            v = PRECISION[v]
-        setattr(prm, k, v)
+        _set(prm, k, v)
     return prm
 
 
@@ -182,9 +207,7 @@ class Context:
         prm = Params()
         C.pointer(prm)[0] = self.params
         for k, v in overrides.items():
-            if k == "precision" and isinstance(v, str):
-                v = PRECISION[v]
-            setattr(prm, k, v)
+            _set(prm, k, v)
         new.params = prm
         new.stream = self.stream
         new._v, new._t, new._f = self._v, self._t, self._f
@@ -206,6 +229,25 @@ class Context:
         out = np.zeros((self.ndens[kind], len(tg)))
         _check(self._lib.bcfmm_direct_sample(self._ctx, t, tg.ctypes.data, len(tg), out.ctypes.data))
         return out
+
+    def mlp_dataset(self, task: str, max_pairs: int) -> dict:
+        """Near-singular pairs of this context (built with near_mode
+        "learned" or "none"), evenly sampled: features, qhat, chat (labels
+        from the FP64 near rule), calibration bins and the (target, source)
+        element indices, as CUDA tensors."""
+        import torch
+        t = {"vtv": 0, "vtb": 1, "btv": 2}[task]
+        feat = torch.empty((max_pairs, 12), dtype=torch.float32, device="cuda")
+        qhat = torch.empty((max_pairs, 16), dtype=torch.float32, device="cuda")
+        chat = torch.empty((max_pairs,), dtype=torch.float32, device="cuda")
+        bins = torch.empty((max_pairs,), dtype=torch.int32, device="cuda")
+        pairs = torch.empty((max_pairs, 2), dtype=torch.int32, device="cuda")
+        n = C.c_int64()
+        _check(self._lib.bcfmm_mlp_dataset(self._ctx, t, max_pairs, C.c_void_p(feat.data_ptr()),
+                                           C.c_void_p(qhat.data_ptr()), C.c_void_p(chat.data_ptr()),
+                                           C.c_void_p(bins.data_ptr()), C.c_void_p(pairs.data_ptr()), C.byref(n)))
+        k = n.value
+        return dict(feat=feat[:k], qhat=qhat[:k], chat=chat[:k], bin=bins[:k], pairs=pairs[:k])
 
     @classmethod
     def from_mesh(cls, mesh, **kw):
@@ -298,3 +340,35 @@ class Context:
         buf = C.create_string_buffer(1 << 16)
         _check(self._lib.bcfmm_stats(self._ctx, buf, len(buf)))
         return json.loads(buf.value.decode())
+
+
+# ------------------------------------------------ learned correction kernels
+def _dev(t):
+    assert t.is_cuda and t.is_contiguous() and t.dtype.is_floating_point and t.element_size() == 4
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s if isinstance(s, int) else s.cuda_stream)
+
+
+def mlp_blob_size() -> int:
+    return int(load().bcfmm_mlp_blob_size())
+
+
+def mlp_grad(params, feat, qhat, chat, grad, loss, stream=None):
+    """grad (6032) and loss (1) of the mean squared error over the pairs."""
+    _check(load().bcfmm_mlp_grad(_dev(params), _dev(feat), _dev(qhat), _dev(chat), feat.shape[0], _dev(grad),
+                                 _dev(loss), _stream_handle(stream)))
+
+
+def mlp_adam(params, grad, m1, m2, step: int, lr: float, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(load().bcfmm_mlp_adam(_dev(params), _dev(grad), _dev(m1), _dev(m2), step, lr, beta1, beta2, eps,
+                                 _stream_handle(stream)))
+
+
+def mlp_predict(params, feat, qhat, out, stream=None):
+    _check(load().bcfmm_mlp_predict(_dev(params), _dev(feat), _dev(qhat), feat.shape[0], _dev(out),
+                                    _stream_handle(stream)))

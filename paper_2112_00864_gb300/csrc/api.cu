@@ -15,6 +15,7 @@
 #include "internal.h"
 #include "kernels.cuh"
 #include "m2l_tc.cuh"
+#include "mlp.cuh"
 
 using namespace bcfmm;
 
@@ -62,7 +63,18 @@ struct DevAlloc {
   }
 };
 
+// Device copies of a task's element geometry kept after the build when the
+// near-singular pairs are classified (training data is drawn from them).
+struct NearGeom {
+  double *tv = nullptr, *sv = nullptr, *tqp = nullptr, *tqw = nullptr, *sqp = nullptr, *sqw = nullptr;
+  double *glx = nullptr, *glw = nullptr;
+  int* row = nullptr;
+  int64_t* ns_list = nullptr;          // CSR positions of the near-singular pairs
+};
+
 struct TaskDev {
+  NearGeom ng{};
+  int64_t n_singular = 0, n_learned = 0, n_fp64 = 0;   // near-pair classes (near_mode != 0)
   DevTaskLists L{};
   std::vector<int> m2m_off, l2l_off;   // host offsets into the per-level arrays
   int* m2m_parent = nullptr;
@@ -86,6 +98,10 @@ struct bcfmm_ctx {
   double *T64 = nullptr, *M2M64 = nullptr, *L2L64 = nullptr;
   float *T32 = nullptr, *M2M32 = nullptr, *L2L32 = nullptr;
   M2LTensorTables tc{};
+  // learned near-singular correction (near_mode 1): per task, FP32 master
+  // parameters and per-bin calibrated errors, from the blob
+  bool mlp_has[3] = {false, false, false};
+  std::vector<float> mlp_params[3], mlp_eps[3];
   // densities
   int ndens[2] = {0, 0}, ndp[2] = {0, 0};
   double* dens[2] = {nullptr, nullptr};
@@ -145,7 +161,7 @@ extern "C" void bcfmm_default_params(bcfmm_params* prm) {
   prm->eta0 = 0.5;
   prm->tc_unit = 0;
   prm->near_mode = 0;
-  prm->mlp_tol = 1e-3;
+  prm->mlp_tol = 5e-3;
   prm->mlp_blob = nullptr;
   prm->mlp_blob_bytes = 0;
 }
@@ -278,7 +294,7 @@ static int upload_task(bcfmm_ctx* C, const HostSetup& H, int t) {
   CU(m.upload(&cor_row, row.data(), row.size(), st));
   CU(m.alloc(&cor_val, T.cor_col.size()));
   L.cor_off = cor_off; L.cor_col = cor_col; L.cor_val = cor_val;
-  {
+  if (C->prm.near_mode == 0) {
     double *tv, *sv, *tqp, *tqw, *sqp, *sqw, *glx, *glw;
     const std::vector<double>& TV = tc == 0 ? H.tet_v : H.tri_v;
     const std::vector<double>& SV = sc == 0 ? H.tet_v : H.tri_v;
@@ -292,12 +308,61 @@ static int upload_task(bcfmm_ctx* C, const HostSetup& H, int t) {
     gauss_legendre01(C->prm.near_n, gx, gw);
     CU(m.upload(&glx, gx.data(), gx.size(), st));
     CU(m.upload(&glw, gw.data(), gw.size(), st));
-    CU(launch_near_rule(t, D.nnz, cor_row, cor_col, tv, sv, tqp, tqw, sqp, sqw, glx, glw, C->prm.near_n,
-                        C->prm.near_k, cor_val, st));
+    CU(launch_near_rule(t, D.nnz, nullptr, cor_row, cor_col, tv, sv, tqp, tqw, sqp, sqw, glx, glw, C->prm.near_n,
+                        C->prm.near_k, 0, cor_val, st));
     CU(cudaStreamSynchronize(st));
     for (void* p : {(void*)tv, (void*)sv, (void*)tqp, (void*)tqw, (void*)sqp, (void*)sqw, (void*)glx, (void*)glw,
                     (void*)cor_row})
       m.release(p);
+  } else {
+    // classify: touching pairs -> FP64 near rule; near-singular pairs ->
+    // learned correction (mode 1, bin accepted), FP64 near rule (mode 1,
+    // bin rejected) or no correction (mode 2)
+    NearGeom& g = D.ng;
+    const std::vector<double>& TV = tc == 0 ? H.tet_v : H.tri_v;
+    const std::vector<double>& SV = sc == 0 ? H.tet_v : H.tri_v;
+    CU(m.upload(&g.tv, TV.data(), TV.size(), st));
+    CU(m.upload(&g.sv, SV.data(), SV.size(), st));
+    CU(m.upload(&g.tqp, H.qp[tc].data(), H.qp[tc].size(), st));
+    CU(m.upload(&g.tqw, H.qw[tc].data(), H.qw[tc].size(), st));
+    CU(m.upload(&g.sqp, H.qp[sc].data(), H.qp[sc].size(), st));
+    CU(m.upload(&g.sqw, H.qw[sc].data(), H.qw[sc].size(), st));
+    std::vector<double> gx, gw;
+    gauss_legendre01(C->prm.near_n, gx, gw);
+    CU(m.upload(&g.glx, gx.data(), gx.size(), st));
+    CU(m.upload(&g.glw, gw.data(), gw.size(), st));
+    g.row = cor_row;
+    const bool learned = C->prm.near_mode == 1 && C->mlp_has[t];
+    float *eps = nullptr, *par = nullptr;
+    if (learned) {
+      CU(m.upload(&eps, C->mlp_eps[t].data(), C->mlp_eps[t].size(), st));
+      CU(m.upload(&par, C->mlp_params[t].data(), C->mlp_params[t].size(), st));
+    }
+    const int64_t cap = std::max<int64_t>(D.nnz, 1);
+    int64_t* lists;
+    unsigned long long* cnt;
+    CU(m.alloc(&lists, 4 * cap));
+    CU(m.alloc(&cnt, 4));
+    CU(cudaMemsetAsync(cnt, 0, 4 * sizeof(unsigned long long), st));
+    CU(cudaMemsetAsync(cor_val, 0, cap * sizeof(double), st));
+    CU(launch_near_classify(t, D.nnz, cor_row, cor_col, g.tv, g.sv, C->prm.near_mode, eps, (float)C->prm.mlp_tol, lists,
+                            cnt, cap, st));
+    unsigned long long hc[4];
+    CU(cudaMemcpyAsync(hc, cnt, sizeof hc, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    D.n_fp64 = (int64_t)hc[0];
+    D.n_learned = (int64_t)hc[1];
+    D.n_singular = (int64_t)hc[3];
+    CU(launch_near_rule(t, D.n_fp64, lists, cor_row, cor_col, g.tv, g.sv, g.tqp, g.tqw, g.sqp, g.sqw, g.glx, g.glw,
+                        C->prm.near_n, C->prm.near_k, 0, cor_val, st));
+    if (learned) CU(launch_near_mlp(t, lists + cap, D.n_learned, cor_row, cor_col, g.tv, g.sv, par, cor_val, st));
+    CU(m.alloc(&g.ns_list, std::max<int64_t>(D.n_singular, 1)));
+    CU(cudaMemcpyAsync(g.ns_list, lists + 3 * cap, D.n_singular * sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
+    CU(cudaStreamSynchronize(st));
+    m.release(lists);
+    m.release(cnt);
+    if (eps) m.release(eps);
+    if (par) m.release(par);
   }
   }
   // counts for the statistics and the roofline
@@ -314,6 +379,34 @@ static int upload_task(bcfmm_ctx* C, const HostSetup& H, int t) {
     D.p2p_pairs += nt * ns;
   }
   return BCFMM_OK;
+}
+
+// Blob of the learned correction: 8 uint32 (magic "BCML" little-endian,
+// version 1, parameters per network, bins, has[3], reserved), then per
+// task t: float params[kMlpParams], float eps[kMlpBins].
+struct MlpBlob {
+  bool has[3] = {false, false, false};
+  std::vector<float> params[3], eps[3];
+};
+constexpr uint32_t kMlpMagic = 0x4C4D4342u;
+constexpr int64_t kMlpBlobBytes = 32 + 3 * (int64_t)(kMlpParams + kMlpBins) * 4;
+
+static std::string parse_mlp_blob(const void* p, int64_t n, MlpBlob& B) {
+  if (!p || n != kMlpBlobBytes) return "near_mode 1 needs an mlp_blob of bcfmm_mlp_blob_size() bytes";
+  uint32_t h[8];
+  std::memcpy(h, p, sizeof h);
+  if (h[0] != kMlpMagic || h[1] != 1 || h[2] != (uint32_t)kMlpParams || h[3] != (uint32_t)kMlpBins)
+    return "mlp_blob header does not match this library's network";
+  const float* f = reinterpret_cast<const float*>(static_cast<const char*>(p) + 32);
+  for (int t = 0; t < 3; ++t) {
+    B.has[t] = h[4 + t] != 0;
+    B.params[t].assign(f, f + kMlpParams);
+    B.eps[t].assign(f + kMlpParams, f + kMlpParams + kMlpBins);
+    for (float v : B.params[t])
+      if (!std::isfinite(v)) return "mlp_blob holds a non-finite parameter";
+    f += kMlpParams + kMlpBins;
+  }
+  return "";
 }
 
 // Host phase of one mesh: element geometry, octree, lists, near pairs.
@@ -360,6 +453,12 @@ static int build_impl(const double* verts, const int64_t* vert_off, const int32_
     return fail(BCFMM_ERR_ARG, "build: unknown precision");
   if (prm.tc_unit < 0 || prm.tc_unit > 4096) return fail(BCFMM_ERR_ARG, "build: tc_unit must be in 0..4096");
   if (prm.near_mode < 0 || prm.near_mode > 2) return fail(BCFMM_ERR_ARG, "build: near_mode must be 0, 1 or 2");
+  MlpBlob blob;
+  if (prm.near_mode == 1 && !reuse) {             // (a rebuild copies the corrections)
+    if (!(prm.mlp_tol > 0)) return fail(BCFMM_ERR_ARG, "build: mlp_tol must be > 0");
+    std::string be = parse_mlp_blob(prm.mlp_blob, prm.mlp_blob_bytes, blob);
+    if (!be.empty()) return fail(BCFMM_ERR_ARG, "build: " + be);
+  }
   const bool tc_mode = prm.precision == BCFMM_FP32_BF16X2 || prm.precision == BCFMM_FP32_BF16X3;
   const int nsplit = prm.precision == BCFMM_FP32_BF16X3 ? 3 : 2;
   if (tc_mode && !m2l_tc_supported(prm.p, nsplit))
@@ -427,6 +526,13 @@ static int build_impl(const double* verts, const int64_t* vert_off, const int32_
     return cleanup(fail(BCFMM_ERR_OOM, "build: device allocation failed (error word)"));
   C->nmesh = nmesh;
   C->reuse = reuse;
+  for (int t = 0; t < 3; ++t) {
+    C->mlp_has[t] = blob.has[t];
+    C->mlp_params[t] = blob.params[t];
+    C->mlp_eps[t] = blob.eps[t];
+  }
+  C->prm.mlp_blob = nullptr;             // read during the build only
+  C->prm.mlp_blob_bytes = 0;
   C->h_verts.assign(verts, verts + 3 * vert_off[nmesh]);
   C->h_tets.assign(tets, tets + 4 * ntet);
   if (ntri > 0) C->h_tris.assign(tris, tris + 3 * ntri);
@@ -902,6 +1008,65 @@ extern "C" int bcfmm_direct_sample(bcfmm_ctx* C, int32_t task, const int64_t* ta
   return BCFMM_OK;
 }
 
+extern "C" int64_t bcfmm_mlp_blob_size(void) { return kMlpBlobBytes; }
+
+extern "C" int bcfmm_mlp_dataset(bcfmm_ctx* C, int32_t task, int64_t max_pairs, float* feat, float* qhat, float* chat,
+                                 int32_t* bin, int32_t* pairs, int64_t* n_out) {
+  if (!C || !feat || !qhat || !chat || !bin || !n_out || max_pairs < 0) return fail(BCFMM_ERR_ARG, "mlp_dataset: null argument");
+  if (task < 0 || task > 2) return fail(BCFMM_ERR_ARG, "mlp_dataset: task must be 0, 1 or 2");
+  *n_out = 0;
+  TaskDev& D = C->task[task];
+  const NearGeom& g = D.ng;
+  if (!g.ns_list) return fail(BCFMM_ERR_STATE, "mlp_dataset: the context was not built with near_mode 1 or 2");
+  const int64_t mcount = std::min(max_pairs, D.n_singular);
+  if (mcount == 0) return BCFMM_OK;
+  cudaStream_t st = C->st;
+  int64_t* sel = nullptr;
+  double *Cv = nullptr, *Q = nullptr;
+  cudaError_t e = cudaMalloc((void**)&sel, mcount * sizeof(int64_t));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&Cv, mcount * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&Q, mcount * sizeof(double));
+  if (e == cudaSuccess) e = launch_select_strided(g.ns_list, D.n_singular, mcount, sel, st);
+  if (e == cudaSuccess)
+    e = launch_pair_data(task, sel, mcount, g.row, D.L.cor_col, g.tv, g.sv, feat, qhat, Q, bin, pairs, st);
+  if (e == cudaSuccess)
+    e = launch_near_rule(task, mcount, sel, g.row, D.L.cor_col, g.tv, g.sv, g.tqp, g.tqw, g.sqp, g.sqw, g.glx, g.glw,
+                         C->prm.near_n, C->prm.near_k, 1, Cv, st);
+  if (e == cudaSuccess) e = launch_label_ratio(Cv, Q, mcount, chat, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(sel);
+  cudaFree(Cv);
+  cudaFree(Q);
+  if (e != cudaSuccess) return fail(BCFMM_ERR_CUDA, std::string("mlp_dataset: ") + cudaGetErrorString(e));
+  *n_out = mcount;
+  return BCFMM_OK;
+}
+
+extern "C" int bcfmm_mlp_grad(const float* params, const float* feat, const float* qhat, const float* chat, int64_t n,
+                              float* grad, float* loss, void* stream) {
+  if (!params || !grad || !loss || n < 0 || (n > 0 && (!feat || !qhat || !chat)))
+    return fail(BCFMM_ERR_ARG, "mlp_grad: null argument");
+  const cudaError_t e = launch_mlp_grad(params, feat, qhat, chat, n, grad, loss, (cudaStream_t)stream);
+  if (e != cudaSuccess) return fail(BCFMM_ERR_CUDA, std::string("mlp_grad: ") + cudaGetErrorString(e));
+  return BCFMM_OK;
+}
+
+extern "C" int bcfmm_mlp_adam(float* params, const float* grad, float* m1, float* m2, int32_t step, float lr,
+                              float beta1, float beta2, float eps, void* stream) {
+  if (!params || !grad || !m1 || !m2 || step < 1) return fail(BCFMM_ERR_ARG, "mlp_adam: bad argument");
+  const cudaError_t e = launch_mlp_adam(params, grad, m1, m2, step, lr, beta1, beta2, eps, (cudaStream_t)stream);
+  if (e != cudaSuccess) return fail(BCFMM_ERR_CUDA, std::string("mlp_adam: ") + cudaGetErrorString(e));
+  return BCFMM_OK;
+}
+
+extern "C" int bcfmm_mlp_predict(const float* params, const float* feat, const float* qhat, int64_t n, float* out,
+                                 void* stream) {
+  if (!params || !out || n < 0 || (n > 0 && (!feat || !qhat))) return fail(BCFMM_ERR_ARG, "mlp_predict: null argument");
+  const cudaError_t e = launch_mlp_predict(params, feat, qhat, n, out, (cudaStream_t)stream);
+  if (e != cudaSuccess) return fail(BCFMM_ERR_CUDA, std::string("mlp_predict: ") + cudaGetErrorString(e));
+  return BCFMM_OK;
+}
+
 extern "C" int bcfmm_stats(const bcfmm_ctx* C, char* json, size_t cap) {
   if (!C || !json) return fail(BCFMM_ERR_ARG, "stats: null argument");
   std::string s = "{";
@@ -918,19 +1083,23 @@ extern "C" int bcfmm_stats(const bcfmm_ctx* C, char* json, size_t cap) {
     kv("device_error", herr);
   }
   kv("p", C->prm.p); kv("np", C->np); kv("eta0", C->prm.eta0); kv("n_offsets", C->ncode); kv("leaf_size", C->prm.leaf_size); kv("precision", C->prm.precision);
+  kv("near_mode", C->prm.near_mode); kv("tc_unit", C->prm.tc_unit);
   kv("nbox", C->nbox); kv("nleaf", C->nleaf); kv("nlevels", C->nlevels);
   kv("nmesh", C->nmesh); kv("host_setup_s", C->sec_host);
   kv("setup_s", C->sec_setup); kv("tree_s", C->sec_tree); kv("lists_s", C->sec_lists);
   kv("near_search_s", C->sec_near_host); kv("near_rule_s", C->sec_near_dev);
   const char* names[3] = {"vtv", "vtb", "btv"};
   for (int t = 0; t < 3; ++t) {
-    char b[400];
+    char b[600];
     snprintf(b, sizeof b,
              "\"%s\": {\"p2p_pairs\": %lld, \"near_boxes\": %lld, \"m2l_pairs\": %lld, \"near_pairs\": %lld, "
-             "\"p2p_leaves\": %d, \"m2l_targets\": %d, \"p2m_leaves\": %d, \"tc_entries\": %lld}, ",
+             "\"p2p_leaves\": %d, \"m2l_targets\": %d, \"p2m_leaves\": %d, \"tc_entries\": %lld, "
+             "\"near_singular\": %lld, \"near_learned\": %lld, \"near_fp64\": %lld}, ",
              names[t], (long long)C->task[t].p2p_pairs, (long long)C->task[t].near_boxes,
              (long long)C->task[t].m2l_pairs, (long long)C->task[t].nnz, C->task[t].L.n_p2p, C->task[t].L.n_m2l,
-             C->task[t].L.n_p2m, (long long)C->task[t].tc_entries);
+             C->task[t].L.n_p2m, (long long)C->task[t].tc_entries, (long long)C->task[t].n_singular,
+             (long long)C->task[t].n_learned,
+             (long long)(C->prm.near_mode == 0 ? C->task[t].nnz : C->task[t].n_fp64));
     s += b;
   }
   // stages: weights+clear, P2M+M2M, M2L, L2L, L2P+P2P, element sums+corrections

@@ -76,11 +76,12 @@ cudaError_t launch_direct_sample(const DevGeom& G, const DevTaskLists& L, const 
                                  int n, const double* dens, int ndens, double* out, cudaStream_t st);
 
 // setup: near-rule corrections C_ts = N_ts - Q_ts (FP64)
-cudaError_t launch_near_rule(int task, int64_t nnz, const int* row, const int* col,
+// (sel: optional list of CSR positions; nnz is then its length)
+cudaError_t launch_near_rule(int task, int64_t nnz, const int64_t* sel, const int* row, const int* col,
                              const double* tgt_v, const double* src_v,
                              const double* tgt_qp, const double* tgt_qw,
                              const double* src_qp, const double* src_qw,
-                             const double* glx, const double* glw, int n, int k,
+                             const double* glx, const double* glw, int n, int k, int compact,
                              double* cor_val, cudaStream_t st);
 
 }  // namespace bcfmm

@@ -149,16 +149,20 @@ __constant__ int c_tri_child[4][3][2] = {
 
 constexpr int kMaxGL = 8;
 
-// One warp per near pair (CSR position k): lanes share the outer points.
-__global__ void k_near_rule(int task, int64_t nnz, const int* __restrict__ row, const int* __restrict__ col,
+// One warp per near pair (CSR position k = sel[i], or i without a
+// selection list): lanes share the outer points.  The result goes to
+// cor_val[k], or to cor_val[i] when compact is set.
+__global__ void k_near_rule(int task, int64_t nnz, const int64_t* __restrict__ sel, const int* __restrict__ row,
+                            const int* __restrict__ col,
                             const double* __restrict__ tgt_v, const double* __restrict__ src_v,
                             const double* __restrict__ tgt_qp, const double* __restrict__ tgt_qw,
                             const double* __restrict__ src_qp, const double* __restrict__ src_qw,
                             const double* __restrict__ glx, const double* __restrict__ glw, int n, int k,
-                            double* __restrict__ cor_val) {
-  const int64_t kk = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+                            int compact, double* __restrict__ cor_val) {
+  const int64_t ii = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (kk >= nnz) return;
+  if (ii >= nnz) return;
+  const int64_t kk = sel ? sel[ii] : ii;
   const int t = row[kk], s = col[kk];
   const bool tgt_tet = (task != 1), src_tet = (task != 2);
   const int nvt = tgt_tet ? 4 : 3, nvs = src_tet ? 4 : 3;
@@ -233,20 +237,20 @@ __global__ void k_near_rule(int task, int64_t nnz, const int* __restrict__ row, 
   double c = sum - q;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-  if (lane == 0) cor_val[kk] = c;
+  if (lane == 0) cor_val[compact ? ii : kk] = c;
 }
 
-cudaError_t launch_near_rule(int task, int64_t nnz, const int* row, const int* col,
+cudaError_t launch_near_rule(int task, int64_t nnz, const int64_t* sel, const int* row, const int* col,
                              const double* tgt_v, const double* src_v,
                              const double* tgt_qp, const double* tgt_qw,
                              const double* src_qp, const double* src_qw,
                              const double* glx, const double* glw, int n, int k,
-                             double* cor_val, cudaStream_t st) {
+                             int compact, double* cor_val, cudaStream_t st) {
   if (nnz == 0) return cudaSuccess;
   if (n > kMaxGL) return cudaErrorInvalidValue;
   const int64_t threads = nnz * 32;
-  k_near_rule<<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(task, nnz, row, col, tgt_v, src_v, tgt_qp, tgt_qw,
-                                                                src_qp, src_qw, glx, glw, n, k, cor_val);
+  k_near_rule<<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(task, nnz, sel, row, col, tgt_v, src_v, tgt_qp, tgt_qw,
+                                                                src_qp, src_qw, glx, glw, n, k, compact, cor_val);
   return cudaGetLastError();
 }
 
