@@ -3,8 +3,9 @@
 Workload (the paper's volume-potential tasks, Sec. 5 / Algorithms 1-2):
 unit ball bounded by the level-4 icosphere (5120 triangles), radially graded
 BC tet mesh (~1.9e5 tets, ~7.7e5 tet quadrature points), density f = 1.
-One step = set_density + eval_vtv + eval_vtb (one pass of the whole hot
-path).  value = (4 ntet + 3 ntri) * ndens / step time, summed over ranks.
+One step = set_density + one CUDA-graph launch of VtV + VtB (one pass of
+the whole hot path; VtB reuses VtV's upward pass).  value = (4 ntet +
+3 ntri) * ndens / step time, summed over ranks.
 
 Accuracy gate: the chosen form is compared with the FP64 CPU oracle (direct
 definition, O1) on sampled target elements; rel L2 error must be <= 1e-6.
@@ -13,6 +14,15 @@ the dominant kernel (live CUDA events on the library's stream) and the CPU
 oracle's throughput on a bounded sample (cpu_baseline).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload ball|batch|learned]
+
+--workload batch: 64 ragged cube/ball BC meshes (h in {1/8, 1/16, 1/32}),
+4 Gaussian-bump densities each, one forest, one graph launch per step, the
+configuration picked by the autotuner on a sample of the meshes.
+--workload learned: unit cube h = 1/64; the near-singular correction
+network trained on random BC meshes, then the build with the learned
+correction against the build with the FP64 near rule (setup time, learned
+fraction, accuracy against the oracle, throughput).
 """
 from __future__ import annotations
 
@@ -140,13 +150,6 @@ def tc_padded_macs_per_row(p):
     return macs
 
 
-def launches_per_step(stats):
-    """Kernels of this library launched by one set_density + eval_vtv + eval_vtb."""
-    L = stats["nlevels"]
-    per_eval = 1 + 1 + L + 1 + max(0, L - 3) + 1 + 1      # weights, P2M, M2M per level, M2L, L2L, P2P+L2P, sums
-    return 2 * per_eval
-
-
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -171,14 +174,19 @@ def run_ours(args):
     f_dev = torch.tensor(f, device="cuda")
     out_v = torch.empty((1, m.ntet), dtype=torch.float64, device="cuda")
     out_b = torch.empty((1, m.ntri), dtype=torch.float64, device="cuda")
+    outs = {"vtv": out_v, "vtb": out_b}
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def step():
         ctx.set_density(bcfmm.VOLUME, f_dev)
+        ctx.eval_graph(("vtv", "vtb"), outs)
+
+    def step_stages():
+        ctx.set_density(bcfmm.VOLUME, f_dev)
         ctx.eval_vtv(out_v)
         ctx.eval_vtb(out_b)
 
-    def timed(fn, K):
+    def timed(fn, K, stages_too=False):
         times, stages = [], []
         for _ in range(K):
             flush.fill_(1.0)                       # L2 flush between timed steps
@@ -189,8 +197,9 @@ def run_ours(args):
             e.record(stream)
             torch.cuda.synchronize()
             times.append(s.elapsed_time(e))
-            st = ctx.stats()["stage_ms"]
-            stages.append((st["vtv"], st["vtb"]))
+            if stages_too:
+                st = ctx.stats()["stage_ms"]
+                stages.append((st["vtv"], st["vtb"]))
         return times, stages
 
     for _ in range(args.warmup):
@@ -200,8 +209,14 @@ def run_ours(args):
         torch.distributed.barrier()
     clocks = ClockSampler(local)
     clocks.start()
-    times, stages = timed(step, args.steps)
+    times, _ = timed(step, args.steps)
     clk = clocks.stop()
+    graph_kernels = int(ctx.stats()["graph_kernels"])
+    # per-stage device times of the same kernels launched one by one (CUDA
+    # events on the library's stream between the stages), for the roofline
+    for _ in range(2):
+        step_stages()
+    stage_times, stages = timed(step_stages, max(3, args.steps // 2), stages_too=True)
     if world > 1:
         torch.distributed.barrier()
     ms = float(np.mean(times))
@@ -218,9 +233,10 @@ def run_ours(args):
     hv_np, hb_np, fh_np = hv.numpy(), hb.numpy(), f_host.numpy()
 
     def step_e2e():
-        ctx.set_density(bcfmm.VOLUME, fh_np)
-        ctx.eval_vtv(hv_np)
-        ctx.eval_vtb(hb_np)
+        ctx.set_density(bcfmm.VOLUME, fh_np)          # pinned host -> device inside the call
+        ctx.eval_graph(("vtv", "vtb"), outs)
+        hv.copy_(out_v)
+        hb.copy_(out_b)
 
     for _ in range(2):
         step_e2e()
@@ -320,7 +336,9 @@ def run_ours(args):
                                        f"elements of the same workload ({osec:.1f} s)"},
             "e2e": {"value": npts / (e2e_ms * 1e-3), "unit": "target pts/s",
                     "h2d_bytes_per_step": int(f.nbytes), "d2h_bytes_per_step": int(8 * (m.ntet + m.ntri))},
-            "gpu_launches": launches_per_step(st) * args.steps,
+            "gpu_launches": graph_kernels * args.steps,
+            "graph": {"kernel_nodes_per_step": graph_kernels,
+                      "stage_pass_ms_per_step": float(np.mean(stage_times))},
             "clocks": clk,
             "setup_s": setup_s,
         }
@@ -329,6 +347,173 @@ def run_ours(args):
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
     return result
+
+
+def _timed_steps(fn, K, stream, flush):
+    import torch
+    times = []
+    for _ in range(K):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        fn()
+        e.record(stream)
+        torch.cuda.synchronize()
+        times.append(s.elapsed_time(e))
+    return times
+
+
+def _sizes(verts, elems):
+    v = verts[elems]
+    n = np.cross(v[:, 1] - v[:, 0], v[:, 2] - v[:, 0])
+    if elems.shape[1] == 3:
+        return 0.5 * np.linalg.norm(n, axis=1)
+    return np.abs(np.einsum("ij,ij->i", n, v[:, 3] - v[:, 0])) / 6
+
+
+def run_batch(args):
+    """Config 3: 64 ragged meshes, 4 densities each, one forest, one graph
+    launch per step; leaf size, p and the M2L work-unit size picked by the
+    autotuner on one mesh of each (kind, h) class."""
+    import torch
+    from paper_2112_00864_gb300 import bcfmm
+    from paper_2112_00864_gb300.autotune import autotune
+    from paper_2112_00864_gb300.build import build
+    from paper_2112_00864_gb300.inputs import batch_meshes, densities
+    import oracle as O
+    build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    meshes = batch_meshes(64, seed=0)
+    F = [densities(m, "bumps", ndens=4, seed=1000 + i)[0] for i, m in enumerate(meshes)]
+    picked, seen = [], set()
+    for i, m in enumerate(meshes):
+        key = (m.name.split("_")[0], m.info.get("h_req"))
+        if key not in seen:
+            seen.add(key)
+            picked.append(i)
+    t0 = time.perf_counter()
+    base = bcfmm.Context.from_meshes([meshes[i] for i in picked], p=4, precision="fp32", stream=stream)
+    best, trials = autotune(base, np.concatenate([F[i] for i in picked], axis=1), tol=1e-6, nsample=128, reps=3)
+    base.close()
+    tune_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ctx = bcfmm.Context.from_meshes(meshes, stream=stream, **best)
+    setup_s = time.perf_counter() - t0
+    Fall = torch.tensor(np.concatenate(F, axis=1), device="cuda")
+    ctx.set_density(bcfmm.VOLUME, Fall)
+    outs = ctx.eval_graph(("vtv", "vtb"))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        ctx.set_density(bcfmm.VOLUME, Fall)
+        ctx.eval_graph(("vtv", "vtb"), outs)
+
+    for _ in range(args.warmup):
+        step()
+    clocks = ClockSampler(0)
+    clocks.start()
+    times = _timed_steps(step, args.steps, stream, flush)
+    clk = clocks.stop()
+    ms = float(np.mean(times))
+    st = ctx.stats()
+    ntet, ntri = ctx.ntet, ctx.ntri
+    npts = (4 * ntet + 3 * ntri) * 4
+    # accuracy: O1 on sampled targets of 8 meshes
+    uv = ctx.split(outs["vtv"].cpu().numpy(), "vtv")
+    ub = ctx.split(outs["vtb"].cpu().numpy(), "vtb")
+    errs = []
+    rng = np.random.default_rng(3)
+    for i in rng.choice(len(meshes), 8, replace=False):
+        m = meshes[i]
+        for t, u, n, el in (("vtv", uv[i], m.ntet, m.tets), ("vtb", ub[i], m.ntri, m.tris)):
+            idx = np.sort(rng.choice(n, 8, replace=False))
+            size = _sizes(m.verts, el[idx])
+            ref = O.direct(t, m, F[i], targets=idx) / size
+            errs.append(float(np.linalg.norm(u[:, idx] / size - ref) / np.linalg.norm(ref)))
+    # plain FP64 on the same batch and tree
+    plain = ctx.build_like(precision="fp64")
+    plain.set_density(bcfmm.VOLUME, Fall)
+    pouts = plain.eval_graph(("vtv", "vtb"))
+    pt = _timed_steps(lambda: (plain.set_density(bcfmm.VOLUME, Fall), plain.eval_graph(("vtv", "vtb"), pouts)),
+                      3, stream, flush)
+    plain.close()
+    return {
+        "metric": METRIC, "value": npts / (ms * 1e-3), "unit": "target pts/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (P2P, expansions, M2L); f64 setup, near corrections, sums",
+        "data": "synthetic: 64 analytic BC meshes, Gaussian-bump densities (no dataset)",
+        "config": {"workload": "batch of 64 cube/ball BC meshes, h in {1/8,1/16,1/32}, 4 bump densities each",
+                   "nmesh": len(meshes), "ntet": int(ntet), "ntri": int(ntri), "ndens": 4,
+                   "l2": "flushed between steps", "autotuned": best},
+        "accuracy": {"rel_l2_vs_oracle_max": max(errs), "samples": len(errs), "ok": bool(max(errs) <= 1e-6)},
+        "plain_fp64": {"value": npts / (float(np.mean(pt)) * 1e-3), "ms_per_step": float(np.mean(pt)),
+                       "chosen_over_plain": float(np.mean(pt)) / ms},
+        "autotune": {"seconds": tune_s, "meshes": len(picked),
+                     "trials": [dict(t.params, ms=t.ms, err=t.err, ok=t.ok) for t in trials]},
+        "gpu_launches": int(st["graph_kernels"]) * args.steps, "clocks": clk, "setup_s": setup_s,
+        "near_pairs": {t: st[t]["near_pairs"] for t in ("vtv", "vtb")},
+    }
+
+
+def run_learned(args):
+    """Config 4: unit cube h = 1/64 with the learned near-singular
+    correction against the FP64 near rule and against no correction."""
+    import torch
+    from paper_2112_00864_gb300 import bcfmm, learned
+    from paper_2112_00864_gb300.build import build
+    from paper_2112_00864_gb300.inputs import cube_bc_mesh, densities
+    import oracle as O
+    build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    blob, rep = learned.train_blob(tasks=("vtv", "vtb"))
+    train_s = time.perf_counter() - t0
+    m = cube_bc_mesh(1 / 64, 1 / 64)
+    f = densities(m, "sine")[0]
+    res = {}
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    rng = np.random.default_rng(8)
+    tv = np.sort(rng.choice(m.ntet, 48, replace=False))
+    tb = np.sort(rng.choice(m.ntri, 48, replace=False))
+    ov = O.direct("vtv", m, f, targets=tv)[0] / _sizes(m.verts, m.tets[tv])
+    ob = O.direct("vtb", m, f, targets=tb)[0] / _sizes(m.verts, m.tris[tb])
+    for mode in ("fp64", "learned", "none"):
+        kw = dict(CHOSEN, near_mode=mode)
+        if mode == "learned":
+            kw.update(mlp_blob=blob)
+        t0 = time.perf_counter()
+        ctx = bcfmm.Context.from_mesh(m, stream=stream, **kw)
+        setup = time.perf_counter() - t0
+        fd = torch.tensor(f, device="cuda")
+        ctx.set_density(bcfmm.VOLUME, fd)
+        outs = ctx.eval_graph(("vtv", "vtb"))
+        for _ in range(args.warmup):
+            ctx.eval_graph(("vtv", "vtb"), outs)
+        times = _timed_steps(lambda: (ctx.set_density(bcfmm.VOLUME, fd), ctx.eval_graph(("vtv", "vtb"), outs)),
+                             args.steps, stream, flush)
+        st = ctx.stats()
+        u_v = outs["vtv"].cpu().numpy()[0][tv] / _sizes(m.verts, m.tets[tv])
+        u_b = outs["vtb"].cpu().numpy()[0][tb] / _sizes(m.verts, m.tris[tb])
+        res[mode] = {"setup_s": setup, "near_rule_s": st["near_rule_s"], "ms_per_step": float(np.mean(times)),
+                     "rel_l2_vs_oracle": {"vtv": float(np.linalg.norm(u_v - ov) / np.linalg.norm(ov)),
+                                          "vtb": float(np.linalg.norm(u_b - ob) / np.linalg.norm(ob))},
+                     "near": {t: {k: st[t][k] for k in ("near_pairs", "near_singular", "near_learned", "near_fp64")}
+                              for t in ("vtv", "vtb")}}
+        ctx.close()
+    npts = 4 * m.ntet + 3 * m.ntri
+    ms = res["learned"]["ms_per_step"]
+    return {
+        "metric": METRIC, "value": npts / (ms * 1e-3), "unit": "target pts/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (P2P, expansions, M2L); learned near-singular corrections BF16 weights / FP32; f64 rest",
+        "data": "synthetic: analytic BC cube mesh, f = 1 + sin sin sin; network trained on random BC meshes",
+        "config": {"workload": "unit cube BC mesh h=1/64 with the learned near-singular correction",
+                   "ntet": int(m.ntet), "ntri": int(m.ntri), **CHOSEN},
+        "training": {"seconds": train_s, **rep}, "modes": res,
+    }
 
 
 def run_reference(args):
@@ -374,9 +559,17 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["ball", "batch", "learned"], default="ball")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
-    res = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if args.impl == "reference":
+        res = run_reference(args)
+    elif args.workload == "batch":
+        res = run_batch(args)
+    elif args.workload == "learned":
+        res = run_learned(args)
+    else:
+        res = run_ours(args)
     if res is not None:
         print(json.dumps(res), flush=True)
 

@@ -11,7 +11,8 @@ launch a user makes (``Context.eval_graph``) and its error is measured on
 sampled target elements against the library's FP64 direct evaluation of
 the discrete operator (``Context.direct_sample``), as the relative L2
 error of cell averages.  The winner is the fastest candidate whose error
-is at most ``tol`` for every task.
+is at most ``safety * tol`` for every task (the sample stands for meshes
+and targets the tuner did not see; the margin covers that).
 """
 from __future__ import annotations
 
@@ -22,7 +23,7 @@ import numpy as np
 
 from . import bcfmm
 
-DEFAULT_SPACE = dict(leaf_size=(32, 64, 128), p=(4, 6, 8), tc_unit=(0, 32))
+DEFAULT_SPACE = dict(leaf_size=(32, 64, 128), p=(4, 5, 6, 7, 8), tc_unit=(0, 32))
 
 
 @dataclass
@@ -76,7 +77,8 @@ def _time_graph(ctx, tasks, outs, reps: int) -> float:
 
 
 def autotune(base: "bcfmm.Context", dens_volume, dens_boundary=None, tasks=("vtv", "vtb"), tol: float = 1e-6,
-             space: dict | None = None, nsample: int = 64, reps: int = 5, seed: int = 0, verbose: bool = False):
+             space: dict | None = None, nsample: int = 64, reps: int = 5, seed: int = 0, safety: float = 0.5,
+             verbose: bool = False):
     """Returns (best params dict, list of Trial).  ``base`` is any context on
     the meshes (its near pairs are reused); densities as for set_density."""
     rng = np.random.default_rng(seed)
@@ -103,7 +105,7 @@ def autotune(base: "bcfmm.Context", dens_volume, dens_boundary=None, tasks=("vtv
                 idx, ref, size = refs[t]
                 u = outs[t].cpu().numpy()[:, idx] / size
                 tr.err[t] = float(np.linalg.norm(u - ref) / np.linalg.norm(ref))
-            tr.ok = all(e <= tol for e in tr.err.values())
+            tr.ok = all(e <= safety * tol for e in tr.err.values())
             ctx.close()
         except bcfmm.BcfmmError as ex:
             tr.note = str(ex)
@@ -112,6 +114,6 @@ def autotune(base: "bcfmm.Context", dens_volume, dens_boundary=None, tasks=("vtv
         trials.append(tr)
     good = [t for t in trials if t.ok]
     if not good:
-        raise RuntimeError(f"autotune: no configuration reaches tol={tol:g}")
+        raise RuntimeError(f"autotune: no configuration reaches {safety:g} * tol = {safety * tol:g}")
     best = min(good, key=lambda t: t.ms)
     return dict(best.params), trials

@@ -906,6 +906,18 @@ extern "C" int bcfmm_eval_graph(bcfmm_ctx* C, int32_t mask, double* out_vtv, dou
     C->prm.timing = timing;
     if (rc != BCFMM_OK) { if (graph) cudaGraphDestroy(graph); return rc; }
     if (ce != cudaSuccess) return fail(BCFMM_ERR_CUDA, std::string("eval_graph: capture failed: ") + cudaGetErrorString(ce));
+    int nkernel = 0;
+    {
+      size_t nn = 0;
+      if (cudaGraphGetNodes(graph, nullptr, &nn) == cudaSuccess && nn > 0) {
+        std::vector<cudaGraphNode_t> nodes(nn);
+        if (cudaGraphGetNodes(graph, nodes.data(), &nn) == cudaSuccess)
+          for (size_t i = 0; i < nn; ++i) {
+            cudaGraphNodeType ty;
+            if (cudaGraphNodeGetType(nodes[i], &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++nkernel;
+          }
+      }
+    }
     const cudaError_t ie = cudaGraphInstantiate(&g.exec, graph, 0);
     cudaGraphDestroy(graph);
     if (ie != cudaSuccess) { g.exec = nullptr; return fail(BCFMM_ERR_CUDA, std::string("eval_graph: instantiate: ") + cudaGetErrorString(ie)); }
@@ -914,7 +926,7 @@ extern "C" int bcfmm_eval_graph(bcfmm_ctx* C, int32_t mask, double* out_vtv, dou
     g.ndens[0] = C->ndens[0];
     g.ndens[1] = C->ndens[1];
     std::copy(outs, outs + 3, g.out);
-    g.nodes = 0;
+    g.nodes = nkernel;
   }
   CU(cudaGraphLaunch(g.exec, C->st));
   C->ev_rec[0] = C->ev_rec[1] = C->ev_rec[2] = false;
@@ -1084,6 +1096,7 @@ extern "C" int bcfmm_stats(const bcfmm_ctx* C, char* json, size_t cap) {
   }
   kv("p", C->prm.p); kv("np", C->np); kv("eta0", C->prm.eta0); kv("n_offsets", C->ncode); kv("leaf_size", C->prm.leaf_size); kv("precision", C->prm.precision);
   kv("near_mode", C->prm.near_mode); kv("tc_unit", C->prm.tc_unit);
+  kv("graph_kernels", C->graph.exec ? C->graph.nodes : 0); kv("graph_mask", C->graph.exec ? C->graph.mask : 0);
   kv("nbox", C->nbox); kv("nleaf", C->nleaf); kv("nlevels", C->nlevels);
   kv("nmesh", C->nmesh); kv("host_setup_s", C->sec_host);
   kv("setup_s", C->sec_setup); kv("tree_s", C->sec_tree); kv("lists_s", C->sec_lists);

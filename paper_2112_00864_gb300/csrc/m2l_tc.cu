@@ -361,7 +361,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(TcArgs args) {
     const int j0 = h * KG;
     const int row_off = (row >> 3) * (int)sbo_a + (row & 7) * 16;
     const uint32_t bbytes = (uint32_t)(NSPLIT * P.bpart_bytes);
-    // drain mapping: TMEM lane quarter = warp % 4, column half by warp
+    // drain mapping: TMEM lane quarter = warp % 4; the 16-column groups of
+    // the window alternate between the two warps of a quarter (dh)
     const uint32_t tq = tmem + ((uint32_t)((warp & 3) * 32) << 16);
     const int dh = (warp - 1) >> 2;
     const int64_t rstride = (int64_t)NSPLIT * P.kpad;    // bf16 per split-moment row
@@ -376,8 +377,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(TcArgs args) {
       if (!r) return false;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-      for (int c = 0; c < NPAD / 2; c += 16) {
-        const uint32_t col = (uint32_t)(dh * (NPAD / 2) + c);
+      for (int gi = dh; gi < NPAD / 16; gi += 2) {      // 16-column groups, alternating halves
+        const uint32_t col = (uint32_t)(gi * 16);
         float dv[16], sh[16], sl[16];
         tmem_ld16(tq + ((wd & 1) ? kColD1 : kColD0) + col, dv);
         if (wd == 0) {
@@ -459,8 +460,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(TcArgs args) {
       if (ok) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-        for (int c = 0; c < NPAD / 2; c += 16) {
-          const uint32_t col = (uint32_t)(dh * (NPAD / 2) + c);
+        for (int gi = dh; gi < NPAD / 16; gi += 2) {
+          const uint32_t col = (uint32_t)(gi * 16);
           float dv[16], sh[16], sl[16];
           tmem_ld16(tq + ((W & 1) ? kColD1 : kColD0) + col, dv);
           if (W == 0) {
@@ -477,7 +478,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(TcArgs args) {
         }
       }
     } else if (ok) {
-      for (int c = 0; c < NPAD / 2; ++c) out[(int64_t)(dh * (NPAD / 2) + c) * kTileM + prow] = make_float2(0.f, 0.f);
+      for (int gi = dh; gi < NPAD / 16; gi += 2)
+        for (int i = 0; i < 16; ++i) out[(int64_t)(gi * 16 + i) * kTileM + prow] = make_float2(0.f, 0.f);
     }
     if (!ok) cp_wait<0>();               // no copy may land after the CTA exits
   }

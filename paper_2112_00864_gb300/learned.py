@@ -52,18 +52,20 @@ def training_meshes(seeds=range(1, 17), max_h_index: int = 3):
     return out
 
 
-def collect(meshes, task: str, per_mesh: int):
-    """Concatenated training data of ``task`` from the meshes (CUDA tensors)."""
+def collect(meshes, tasks, per_mesh: int):
+    """Training data per task from the meshes: {task: dict of CUDA tensors}.
+    Each mesh is built once (near_mode "none") and serves every task."""
     import torch
-    parts = []
+    parts = {t: [] for t in tasks}
     for m in meshes:
-        if task != "vtv" and m.ntri == 0:
-            continue
         ctx = bcfmm.Context.from_mesh(m, p=2, leaf_size=64, precision="fp32", near_mode="none")
-        d = ctx.mlp_dataset(task, per_mesh)
-        parts.append({k: v.clone() for k, v in d.items() if k != "pairs"})
+        for t in tasks:
+            if t != "vtv" and m.ntri == 0:
+                continue
+            d = ctx.mlp_dataset(t, per_mesh)
+            parts[t].append({k: v.clone() for k, v in d.items() if k != "pairs"})
         ctx.close()
-    return {k: torch.cat([p[k] for p in parts]) for k in ("feat", "qhat", "chat", "bin")}
+    return {t: {k: torch.cat([p[k] for p in parts[t]]) for k in ("feat", "qhat", "chat", "bin")} for t in tasks}
 
 
 def init_params(seed: int = 0) -> np.ndarray:
@@ -161,10 +163,12 @@ def train_blob(tasks=TASKS, seeds=range(1, 17), pairs_per_task: int = 2_000_000,
     import torch
     meshes = training_meshes(seeds, max_h_index)
     nets, report = {}, {}
+    t0 = time.time()
+    alldata = collect(meshes, tasks, max(1, pairs_per_task // len(meshes)))
+    torch.cuda.synchronize()
+    data_s = time.time() - t0
     for t in tasks:
-        t0 = time.time()
-        data = collect(meshes, t, max(1, pairs_per_task // len(meshes)))
-        torch.cuda.synchronize()
+        data = alldata[t]
         t1 = time.time()
         tr, val = split(data)
         params, hist = train(tr, steps=steps, batch=batch, lr=lr, verbose=verbose)
@@ -172,7 +176,7 @@ def train_blob(tasks=TASKS, seeds=range(1, 17), pairs_per_task: int = 2_000_000,
         t2 = time.time()
         eps, summ = calibrate(params, val)
         nets[t] = (params.cpu().numpy(), eps)
-        report[t] = dict(pairs=int(data["chat"].shape[0]), data_s=t1 - t0, train_s=t2 - t1, steps=steps,
+        report[t] = dict(pairs=int(data["chat"].shape[0]), data_s=data_s, train_s=t2 - t1, steps=steps,
                          loss=hist[-1], bins_accepted_at_5e3=int(np.sum(eps <= 5e-3)), **summ)
         if verbose:
             print(t, report[t], flush=True)

@@ -86,7 +86,7 @@ def test_autotune_pick_meets_tolerance(bc):
             size = O.element_areas(m)[idx] if t == "vtb" else O.element_volumes(m)[idx]
             ref = O.direct(t, m, f, targets=idx) / size
             errs.append(np.linalg.norm(u[:, idx] / size - ref) / np.linalg.norm(ref))
-        assert max(errs) <= 2 * tol, (t, errs)
+        assert max(errs) <= tol, (t, errs)
 
 
 def test_direct_sample_in_a_batch_sees_own_mesh_only(bc):

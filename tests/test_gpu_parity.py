@@ -91,6 +91,28 @@ def test_tensor_core_m2l_matches_oracle(bc, c1, prec, task):
     assert r2 <= 1.5e-6, (r2, rm)
 
 
+@pytest.mark.parametrize("p,prec", [(2, "bf16x2"), (3, "bf16x2"), (4, "bf16x2"), (5, "bf16x2"), (7, "bf16x2"),
+                                    (2, "bf16x3"), (4, "bf16x3"), (5, "bf16x3")])
+def test_tensor_core_m2l_every_order(bc, c1, p, prec):
+    """Every padded width of the tensor-core M2L (16, 32, 48, 64, 96, 128
+    columns for p = 2..7) against the FP64 path at the same p: the
+    difference is the split-precision error alone.  Surface sources (BtV)
+    need the 3-term split, as at p = 6; the 2-term split is checked on the
+    volume-source tasks."""
+    m, f, g = c1
+    legs = ((("vtv", f, bc.VOLUME), ("vtb", f, bc.VOLUME)) if prec == "bf16x2" else
+            (("vtv", f, bc.VOLUME), ("btv", g, bc.BOUNDARY)))
+    for task, dens, kind in legs:
+        u = {}
+        for pr in (prec, "fp64"):
+            ctx = bc.Context.from_mesh(m, p=p, leaf_size=32, precision=pr)
+            ctx.set_density(kind, dens)
+            u[pr] = ctx.eval(task).cpu().numpy()
+            assert ctx.stats()["device_error"] == 0
+        r2, rm = rel(u[prec], u["fp64"], _sizes(m, task))
+        assert r2 <= 1e-6, (task, p, prec, r2, rm)
+
+
 def test_multiple_densities_and_device_io(bc, c1):
     m, f, g = c1
     rng = np.random.default_rng(7)
