@@ -42,6 +42,13 @@ sys.path.insert(0, ROOT)
 METRIC = "VtV+VtB target pts/s at rel err ≤1e-6: chosen form vs plain FP64, 1 GB300"
 WORKLOAD = {"workload": "unit ball BC mesh: icosphere level 4 (5120 triangles), radially graded tets, f=1",
             "mesh": "ball_bc_mesh(level=4, radial=0.35)"}
+
+
+def workload():
+    if BALL_LEVEL == 4:
+        return dict(WORKLOAD)
+    return {"workload": f"unit ball BC mesh: icosphere level {BALL_LEVEL}, radially graded tets, f=1 (small case)",
+            "mesh": f"ball_bc_mesh(level={BALL_LEVEL}, radial=0.35)"}
 CHOSEN = dict(p=6, eta0=0.5, leaf_size=128, precision="bf16x2")
 PLAIN = dict(p=6, eta0=0.5, leaf_size=128, precision="fp64")
 SAMPLE_TARGETS = 64        # per task, for the accuracy gate and the CPU baseline
@@ -108,9 +115,12 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+BALL_LEVEL = 4             # icosphere level of the workload (3 gives a small case for profiling)
+
+
 def make_inputs():
     from paper_2112_00864_gb300.inputs import ball_bc_mesh
-    m = ball_bc_mesh(4, radial=0.35)
+    m = ball_bc_mesh(BALL_LEVEL, radial=0.35)
     f = np.ones((1, m.ntet))
     return m, f
 
@@ -318,7 +328,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 (P2P, expansions, M2L); f64 setup, near corrections, sums",
             "data": "synthetic: analytic BC mesh and density (no dataset)",
-            "config": dict(WORKLOAD, ntet=m.ntet, ntri=m.ntri, ndens=int(f.shape[0]), l2="flushed between steps",
+            "config": dict(workload(), ntet=m.ntet, ntri=m.ntri, ndens=int(f.shape[0]), l2="flushed between steps",
                            **{k: v for k, v in CHOSEN.items()}),
             "accuracy": {"rel_l2_vs_oracle": {k: v[0] for k, v in err.items()},
                          "rel_max_vs_oracle": {k: v[1] for k, v in err.items()},
@@ -546,7 +556,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic: analytic BC mesh and density (no dataset)",
-        "config": dict(WORKLOAD, ntet=m.ntet, ntri=m.ntri, ndens=1, l2="n/a (CPU)"),
+        "config": dict(workload(), ntet=m.ntet, ntri=m.ntri, ndens=1, l2="n/a (CPU)"),
         "cpu_baseline": {"value": value, "unit": "target pts/s", "cores": cores, "kind": "oracle",
                          "sample": f"{per} VtV + {per} VtB random target elements per step (O1, FP64)"},
         "e2e": {"value": value, "unit": "target pts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -560,7 +570,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["ball", "batch", "learned"], default="ball")
+    ap.add_argument("--ball-level", type=int, default=4, help="icosphere level of the ball workload (profiling: 3)")
     args = ap.parse_args()
+    global BALL_LEVEL
+    BALL_LEVEL = args.ball_level
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
     if args.impl == "reference":
         res = run_reference(args)

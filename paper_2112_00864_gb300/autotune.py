@@ -3,8 +3,9 @@ accuracy target on the caller's own meshes and densities.
 
 Search space (all of it is cheap to try because ``Context.build_like``
 copies the near pairs and their FP64 corrections instead of recomputing
-them): leaf size, expansion order p with the precision the tensor-core
-M2L allows for it (BF16 hi+lo split for p <= 7, FP32 on CUDA cores above),
+them): leaf size, expansion order p with the precisions the tensor-core M2L
+allows for it (BF16 hi+lo split for p <= 7, hi+mid+lo for p <= 6, FP32 on
+CUDA cores above),
 and the tensor-core work-unit size ("tile" of the M2L launch: interaction
 entries per CTA).  Each candidate is timed with CUDA events as the graph
 launch a user makes (``Context.eval_graph``) and its error is measured on
@@ -35,18 +36,23 @@ class Trial:
     note: str = ""
 
 
-def _precision_for(p: int) -> str:
-    return "bf16x2" if p <= 7 else "fp32"
+def _precisions_for(p: int):
+    """Precisions the tensor-core M2L offers at order p: the 2-term BF16
+    split up to p = 7, the 3-term split up to p = 6; FP32 on CUDA cores
+    above."""
+    if p <= 6:
+        return ("bf16x2", "bf16x3")
+    return ("bf16x2",) if p <= 7 else ("fp32",)
 
 
 def candidates(space: dict | None = None):
     space = dict(DEFAULT_SPACE, **(space or {}))
     out = []
     for ls, p in itertools.product(space["leaf_size"], space["p"]):
-        prec = _precision_for(p)
-        units = space["tc_unit"] if prec.startswith("bf16") else (0,)
-        for u in units:
-            out.append(dict(leaf_size=int(ls), p=int(p), precision=prec, tc_unit=int(u)))
+        for prec in _precisions_for(p):
+            units = space["tc_unit"] if prec == "bf16x2" else (0,)
+            for u in units:
+                out.append(dict(leaf_size=int(ls), p=int(p), precision=prec, tc_unit=int(u)))
     return out
 
 

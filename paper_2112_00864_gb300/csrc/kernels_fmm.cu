@@ -454,6 +454,184 @@ __global__ void __launch_bounds__(128) k_p2p_l2p_f32(DevGeom G, DevTaskLists L, 
 
 
 
+// Packed form for ND <= 2: two targets per thread and source points taken
+// two at a time, every arithmetic instruction on a float2 (the two sources
+// of a pair: __fadd2_rn / __fmul2_rn / __ffma2_rn), so a target keeps two
+// independent partial sums and the instructions issued per point pair
+// nearly halve.  Source coordinates are staged negated in shared memory
+// (x_t + (-y) needs no separate negation); an odd tile is padded with a
+// weightless point at -1e30, whose distance overflows to inf (rsqrt 0).
+template <int ND>
+__global__ void __launch_bounds__(128) k_p2p_l2p_f32x2(DevGeom G, DevTaskLists L, const float* __restrict__ W,
+                                                       int64_t nsp, int64_t ntp, int ndp,
+                                                       const float* __restrict__ loc, double* __restrict__ phi) {
+  static_assert(ND >= 1 && ND <= 2, "packed P2P serves one or two densities");
+  constexpr int TPT = 2;
+  constexpr int PPT = kTile / 128;
+  __shared__ __align__(16) float sx[2][kTile];
+  __shared__ __align__(16) float sy[2][kTile];
+  __shared__ __align__(16) float sz[2][kTile];
+  __shared__ __align__(16) float sw[2][ND][kTile];
+  __shared__ int pre[kRunBatch + 1], rst[kRunBatch];
+  __shared__ float2 red[ND][128 * TPT];
+  const int b = blockIdx.x;
+  const int leaf = L.p2p_leaf[b];
+  const int sc = L.src_cls, tc = L.tgt_cls;
+  const double4_32a cs = G.box_cs[leaf];
+  float chx, clx, chy, cly, chz, clz;
+  split_df(cs.x, chx, clx); split_df(cs.y, chy, cly); split_df(cs.z, chz, clz);
+  const int2 tr = G.box_rng[tc][leaf];
+  const int nt = tr.y - tr.x;
+  const int TS = (nt + TPT - 1) / TPT;
+  const int NG = 128 / TS;
+  const int ts = threadIdx.x % TS, gi_raw = threadIdx.x / TS;
+  const int gi = gi_raw < NG ? gi_raw : NG;
+  float xt[TPT], yt[TPT], zt[TPT];
+  float2 X[TPT], Y[TPT], Z[TPT];
+  bool act[TPT];
+#pragma unroll
+  for (int u = 0; u < TPT; ++u) {
+    const int t = ts + u * TS;
+    act[u] = t < nt;
+    xt[u] = yt[u] = zt[u] = 1e30f;
+    if (act[u]) {
+      const float4 h = G.pthi[tc][tr.x + t], l = G.ptlo[tc][tr.x + t];
+      xt[u] = (h.x - chx) + (l.x - clx);
+      yt[u] = (h.y - chy) + (l.y - cly);
+      zt[u] = (h.z - chz) + (l.z - clz);
+    }
+    X[u] = make_float2(xt[u], xt[u]);
+    Y[u] = make_float2(yt[u], yt[u]);
+    Z[u] = make_float2(zt[u], zt[u]);
+  }
+  float shi[TPT][ND], slo[TPT][ND];
+#pragma unroll
+  for (int u = 0; u < TPT; ++u)
+#pragma unroll
+    for (int d = 0; d < ND; ++d) shi[u][d] = slo[u][d] = 0.f;
+  const int r0 = L.run_off[b], r1 = L.run_off[b + 1];
+  const int self_len = L.self_len[b];
+  float4 reg[PPT];
+  float regw[PPT];
+  for (int rb = r0; rb < r1; rb += kRunBatch) {
+    const int nr = min(kRunBatch, r1 - rb);
+    __syncthreads();
+    scan_runs(L.runs + rb, nr, pre, rst);
+    __syncthreads();
+    const int total = pre[nr];
+    const int ntiles = (total + kTile - 1) / kTile;
+    auto load_tile = [&](int t) {
+#pragma unroll
+      for (int q = 0; q < PPT; ++q) {
+        const int v = t * kTile + threadIdx.x + q * 128;
+        reg[q] = make_float4(1e30f, 1e30f, 1e30f, 0.f);     // negated padding point
+        regw[q] = 0.f;
+        if (v < total) {
+          const int r = find_run(pre, nr, v);
+          const int src = rst[r] + (v - pre[r]);
+          const float4 h = G.pthi[sc][src], l = G.ptlo[sc][src];
+          reg[q] = make_float4(-((h.x - chx) + (l.x - clx)), -((h.y - chy) + (l.y - cly)),
+                               -((h.z - chz) + (l.z - clz)), W[src]);
+          if (ND > 1) regw[q] = W[nsp + src];
+        }
+      }
+    };
+    auto store_tile = [&](int buf) {
+#pragma unroll
+      for (int q = 0; q < PPT; ++q) {
+        const int j = threadIdx.x + q * 128;
+        sx[buf][j] = reg[q].x;
+        sy[buf][j] = reg[q].y;
+        sz[buf][j] = reg[q].z;
+        sw[buf][0][j] = reg[q].w;
+        if (ND > 1) sw[buf][ND - 1][j] = regw[q];
+      }
+    };
+    if (ntiles > 0) {
+      load_tile(0);
+      store_tile(0);
+    }
+    __syncthreads();
+    for (int t = 0; t < ntiles; ++t) {
+      const int cur = t & 1;
+      if (t + 1 < ntiles) load_tile(t + 1);
+      const int m = min(kTile, total - t * kTile);
+      const int mp = (m + 1) >> 1;
+      float2 acc[TPT][ND];
+#pragma unroll
+      for (int u = 0; u < TPT; ++u)
+#pragma unroll
+        for (int d = 0; d < ND; ++d) acc[u][d] = make_float2(0.f, 0.f);
+      const int kstart = gi_raw < NG ? gi : mp;
+      const float2* px = reinterpret_cast<const float2*>(sx[cur]);
+      const float2* py = reinterpret_cast<const float2*>(sy[cur]);
+      const float2* pz = reinterpret_cast<const float2*>(sz[cur]);
+      if (rb == r0 && t * kTile < self_len) {
+        for (int k = kstart; k < mp; k += NG) {
+          const float2 nx = px[k], ny = py[k], nz = pz[k];
+#pragma unroll
+          for (int u = 0; u < TPT; ++u) {
+            const float2 dx = __fadd2_rn(X[u], nx), dy = __fadd2_rn(Y[u], ny), dz = __fadd2_rn(Z[u], nz);
+            const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+            const float2 ri = make_float2(r2.x > 0.f ? rsqrtf(r2.x) : 0.f, r2.y > 0.f ? rsqrtf(r2.y) : 0.f);
+#pragma unroll
+            for (int d = 0; d < ND; ++d)
+              acc[u][d] = __ffma2_rn(reinterpret_cast<const float2*>(sw[cur][d])[k], ri, acc[u][d]);
+          }
+        }
+      } else {
+#pragma unroll 4
+        for (int k = kstart; k < mp; k += NG) {
+          const float2 nx = px[k], ny = py[k], nz = pz[k];
+#pragma unroll
+          for (int u = 0; u < TPT; ++u) {
+            const float2 dx = __fadd2_rn(X[u], nx), dy = __fadd2_rn(Y[u], ny), dz = __fadd2_rn(Z[u], nz);
+            const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+            const float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+#pragma unroll
+            for (int d = 0; d < ND; ++d)
+              acc[u][d] = __ffma2_rn(reinterpret_cast<const float2*>(sw[cur][d])[k], ri, acc[u][d]);
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < TPT; ++u)
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+          two_sum_f(shi[u][d], slo[u][d], acc[u][d].x);
+          two_sum_f(shi[u][d], slo[u][d], acc[u][d].y);
+        }
+      if (t + 1 < ntiles) store_tile(cur ^ 1);
+      __syncthreads();
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < TPT; ++u)
+#pragma unroll
+    for (int d = 0; d < ND; ++d) red[d][u * 128 + threadIdx.x] = make_float2(shi[u][d], slo[u][d]);
+  __syncthreads();
+  if (gi_raw == 0) {
+#pragma unroll
+    for (int u = 0; u < TPT; ++u) {
+      if (!act[u]) continue;
+      double near[ND];
+#pragma unroll
+      for (int d = 0; d < ND; ++d) {
+        float hi = 0.f, lo = 0.f;
+        for (int g = 0; g < NG; ++g) {
+          const float2 v = red[d][u * 128 + g * TS + ts];
+          two_sum_f(hi, lo, v.x);
+          lo += v.y;
+        }
+        near[d] = (double)hi + (double)lo;
+      }
+      const double inv_s = 1.0 / cs.w;
+      l2p_and_store<float, ND>(G, leaf, ndp, loc, xt[u] * inv_s, yt[u] * inv_s, zt[u] * inv_s, near, tr.x + ts + u * TS,
+                               ntp, phi);
+    }
+  }
+}
+
 template <int ND>
 __global__ void __launch_bounds__(128) k_p2p_l2p_f64(DevGeom G, DevTaskLists L, const double* __restrict__ W,
                                                      int64_t nsp, int64_t ntp, int ndp,
@@ -544,7 +722,14 @@ __global__ void __launch_bounds__(128) k_p2p_l2p_f64(DevGeom G, DevTaskLists L, 
 cudaError_t launch_p2p_l2p_f32(const DevGeom& G, const DevTaskLists& L, const float* W, int64_t nsrc_pts,
                                int64_t ntgt_pts, int ndp, const float* loc, double* phi, cudaStream_t st) {
   if (L.n_p2p == 0) return cudaSuccess;
-  P2P_DISPATCH(k_p2p_l2p_f32, G, L, W, nsrc_pts, ntgt_pts, ndp, loc, phi);
+  switch (ndp) {
+    case 1: k_p2p_l2p_f32x2<1><<<L.n_p2p, 128, 0, st>>>(G, L, W, nsrc_pts, ntgt_pts, ndp, loc, phi); break;
+    case 2: k_p2p_l2p_f32x2<2><<<L.n_p2p, 128, 0, st>>>(G, L, W, nsrc_pts, ntgt_pts, ndp, loc, phi); break;
+    case 4: k_p2p_l2p_f32<4><<<L.n_p2p, 128, 0, st>>>(G, L, W, nsrc_pts, ntgt_pts, ndp, loc, phi); break;
+    case 8: k_p2p_l2p_f32<8><<<L.n_p2p, 128, 0, st>>>(G, L, W, nsrc_pts, ntgt_pts, ndp, loc, phi); break;
+    case 16: k_p2p_l2p_f32<16><<<L.n_p2p, 128, 0, st>>>(G, L, W, nsrc_pts, ntgt_pts, ndp, loc, phi); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

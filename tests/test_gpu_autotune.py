@@ -69,7 +69,8 @@ def test_autotune_pick_meets_tolerance(bc):
     tol = 1e-6
     space = dict(leaf_size=(32, 128), p=(4, 6, 8), tc_unit=(0, 16))
     best, trials = autotune(base, F, tasks=("vtv", "vtb"), tol=tol, space=space, nsample=48, reps=3)
-    assert len(trials) == 2 * (2 * 2 + 1)
+    # per leaf size: p = 4, 6 with bf16x2 (2 unit sizes) and bf16x3, p = 8 with fp32
+    assert len(trials) == 2 * (2 * 3 + 1)
     chosen = [t for t in trials if t.params == best][0]
     assert chosen.ok and chosen.ms == min(t.ms for t in trials if t.ok)
     # the pick against the oracle's O1 on sampled targets of every mesh
