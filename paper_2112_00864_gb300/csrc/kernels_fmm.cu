@@ -454,19 +454,21 @@ __global__ void __launch_bounds__(128) k_p2p_l2p_f32(DevGeom G, DevTaskLists L, 
 
 
 
-// Packed form for ND <= 2: two targets per thread and source points taken
-// two at a time, every arithmetic instruction on a float2 (the two sources
+// Packed form for ND <= 2: TPT targets per thread (4 for one density, 2
+// for two) and source points taken two at a time, every arithmetic instruction on a float2 (the two sources
 // of a pair: __fadd2_rn / __fmul2_rn / __ffma2_rn), so a target keeps two
 // independent partial sums and the instructions issued per point pair
 // nearly halve.  Source coordinates are staged negated in shared memory
 // (x_t + (-y) needs no separate negation); an odd tile is padded with a
 // weightless point at -1e30, whose distance overflows to inf (rsqrt 0).
-template <int ND>
+constexpr int kTileX2 = 512;     // source points per tile of the packed kernel
+
+template <int ND, int TPT>
 __global__ void __launch_bounds__(128) k_p2p_l2p_f32x2(DevGeom G, DevTaskLists L, const float* __restrict__ W,
                                                        int64_t nsp, int64_t ntp, int ndp,
                                                        const float* __restrict__ loc, double* __restrict__ phi) {
   static_assert(ND >= 1 && ND <= 2, "packed P2P serves one or two densities");
-  constexpr int TPT = 2;
+  constexpr int kTile = kTileX2;
   constexpr int PPT = kTile / 128;
   __shared__ __align__(16) float sx[2][kTile];
   __shared__ __align__(16) float sy[2][kTile];
@@ -723,8 +725,8 @@ cudaError_t launch_p2p_l2p_f32(const DevGeom& G, const DevTaskLists& L, const fl
                                int64_t ntgt_pts, int ndp, const float* loc, double* phi, cudaStream_t st) {
   if (L.n_p2p == 0) return cudaSuccess;
   switch (ndp) {
-    case 1: k_p2p_l2p_f32x2<1><<<L.n_p2p, 128, 0, st>>>(G, L, W, nsrc_pts, ntgt_pts, ndp, loc, phi); break;
-    case 2: k_p2p_l2p_f32x2<2><<<L.n_p2p, 128, 0, st>>>(G, L, W, nsrc_pts, ntgt_pts, ndp, loc, phi); break;
+    case 1: k_p2p_l2p_f32x2<1, 4><<<L.n_p2p, 128, 0, st>>>(G, L, W, nsrc_pts, ntgt_pts, ndp, loc, phi); break;
+    case 2: k_p2p_l2p_f32x2<2, 2><<<L.n_p2p, 128, 0, st>>>(G, L, W, nsrc_pts, ntgt_pts, ndp, loc, phi); break;
     case 4: k_p2p_l2p_f32<4><<<L.n_p2p, 128, 0, st>>>(G, L, W, nsrc_pts, ntgt_pts, ndp, loc, phi); break;
     case 8: k_p2p_l2p_f32<8><<<L.n_p2p, 128, 0, st>>>(G, L, W, nsrc_pts, ntgt_pts, ndp, loc, phi); break;
     case 16: k_p2p_l2p_f32<16><<<L.n_p2p, 128, 0, st>>>(G, L, W, nsrc_pts, ntgt_pts, ndp, loc, phi); break;
