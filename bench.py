@@ -19,6 +19,8 @@ oracle's throughput on a bounded sample (cpu_baseline).
 --workload batch: 64 ragged cube/ball BC meshes (h in {1/8, 1/16, 1/32}),
 4 Gaussian-bump densities each, one forest, one graph launch per step, the
 configuration picked by the autotuner on a sample of the meshes.
+--workload largest: unit cube h = 1/32, 1/64, 1/128, VtV + VtB + BtV at
+p = 8 with the learned near field, accuracy per h and observed convergence.
 --workload learned: unit cube h = 1/64; the near-singular correction
 network trained on random BC meshes, then the build with the learned
 correction against the build with the FP64 near rule (setup time, learned
@@ -526,6 +528,81 @@ def run_learned(args):
     }
 
 
+def run_largest(args):
+    """Config 5: unit cube at h = 1/32, 1/64, 1/128 with f = exp(-|x-c|^2/0.05)
+    and g = cos 2 pi x cos 2 pi y cos 2 pi z; VtV + VtB + BtV at p = 8 (FP32 on
+    CUDA cores: the tensor-core M2L stops at p = 7) with the learned
+    near-singular correction for VtV and VtB.  Per h: setup, step time, accuracy against O1
+    on sampled targets; across h: the observed convergence of the energies
+    sum_t f_t u_t (VtV) and sum_t g-driven u_t f_t (BtV)."""
+    import torch
+    from paper_2112_00864_gb300 import bcfmm, learned
+    from paper_2112_00864_gb300.build import build
+    from paper_2112_00864_gb300.inputs import cube_bc_mesh, densities
+    import oracle as O
+    build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    # networks for the volume-source tasks; BtV keeps the FP64 near rule (a
+    # surface source's near pairs carry a large share of u, and the BtV
+    # network at the default tolerance leaves ~1e-5)
+    blob, rep = learned.train_blob(tasks=("vtv", "vtb"))
+    train_s = time.perf_counter() - t0
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    prm = dict(p=8, eta0=0.5, leaf_size=128, precision="fp32", near_mode="learned", mlp_blob=blob)
+    levels, energies = [], []
+    for inv_h in (32, 64, 128):
+        m = cube_bc_mesh(1 / inv_h, 1 / inv_h)
+        f, g = densities(m, "gauss")
+        t0 = time.perf_counter()
+        ctx = bcfmm.Context.from_mesh(m, stream=stream, **prm)
+        setup = time.perf_counter() - t0
+        fd, gd = torch.tensor(f, device="cuda"), torch.tensor(g, device="cuda")
+        ctx.set_density(bcfmm.VOLUME, fd)
+        ctx.set_density(bcfmm.BOUNDARY, gd)
+        tasks = ("vtv", "vtb", "btv")
+        outs = ctx.eval_graph(tasks)
+        for _ in range(args.warmup):
+            ctx.eval_graph(tasks, outs)
+        times = _timed_steps(lambda: (ctx.set_density(bcfmm.VOLUME, fd), ctx.set_density(bcfmm.BOUNDARY, gd),
+                                      ctx.eval_graph(tasks, outs)), args.steps, stream, flush)
+        st = ctx.stats()
+        u = {t: outs[t].cpu().numpy()[0] for t in tasks}
+        rng = np.random.default_rng(inv_h)
+        acc = {}
+        for t, dens, n, el in (("vtv", f, m.ntet, m.tets), ("vtb", f, m.ntri, m.tris), ("btv", g, m.ntet, m.tets)):
+            idx = np.sort(rng.choice(n, 32, replace=False))
+            size = _sizes(m.verts, el[idx])
+            ref = O.direct(t, m, dens, targets=idx)[0] / size
+            acc[t] = float(np.linalg.norm(u[t][idx] / size - ref) / np.linalg.norm(ref))
+        energies.append((float(np.dot(f[0], u["vtv"])), float(np.dot(f[0], u["btv"]))))
+        ms = float(np.mean(times))
+        npts = 4 * m.ntet + 3 * m.ntri + 4 * m.ntet
+        levels.append({"h": f"1/{inv_h}", "ntet": int(m.ntet), "ntri": int(m.ntri), "setup_s": setup,
+                       "near_rule_s": st["near_rule_s"], "ms_per_step": ms, "target_pts_per_s": npts / (ms * 1e-3),
+                       "rel_l2_vs_oracle": acc,
+                       "near_learned_fraction": {t: st[t]["near_learned"] / max(1, st[t]["near_pairs"]) for t in tasks}})
+        ctx.close()
+        del outs
+        torch.cuda.empty_cache()
+    rates = {}
+    for k, name in ((0, "vtv_energy"), (1, "btv_energy")):
+        e = [x[k] for x in energies]
+        d1, d2 = abs(e[0] - e[1]), abs(e[1] - e[2])
+        rates[name] = {"values": e, "observed_order": float(math.log2(d1 / d2)) if d2 > 0 else None}
+    big = levels[-1]
+    return {
+        "metric": METRIC, "value": big["target_pts_per_s"], "unit": "target pts/s (VtV + VtB + BtV)", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": big["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (P2P, expansions, M2L); learned near-singular; f64 rest",
+        "data": "synthetic: analytic BC cube meshes, Gaussian f, cosine g",
+        "config": {"workload": "unit cube BC meshes h = 1/32, 1/64, 1/128; VtV+VtB+BtV; p = 8 FP32, learned near field",
+                   **{k: v for k, v in prm.items() if k != "mlp_blob"}},
+        "levels": levels, "convergence": rates, "training_s": train_s,
+    }
+
+
 def run_reference(args):
     """The oracle arm: O1 (FP64 CPU direct definition) on bounded samples of
     the same workload, timed per step on the host cores."""
@@ -569,7 +646,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["ball", "batch", "learned"], default="ball")
+    ap.add_argument("--workload", choices=["ball", "batch", "learned", "largest"], default="ball")
     ap.add_argument("--ball-level", type=int, default=4, help="icosphere level of the ball workload (profiling: 3)")
     args = ap.parse_args()
     global BALL_LEVEL
@@ -581,6 +658,8 @@ def main():
         res = run_batch(args)
     elif args.workload == "learned":
         res = run_learned(args)
+    elif args.workload == "largest":
+        res = run_largest(args)
     else:
         res = run_ours(args)
     if res is not None:
