@@ -321,6 +321,18 @@ void bcfmm_destroy(bcfmm_ctx* ctx);
  */
 int bcfmm_debug_m2l_matrix(int32_t p, const double* o, double* T);
 
+/*
+ * Test hook for the failure path of the bounded device waits (the paper has
+ * no counterpart): enqueues on the context's stream one thread that waits,
+ * through the same bounded mbarrier wait the tensor-core M2L uses, on a
+ * barrier whose expected arrival never comes, giving up after `spins`
+ * polls (1..2^20).  It then sets the context's device error word, exactly
+ * as an expired wait inside an evaluation would: the next evaluation with
+ * host output returns BCFMM_ERR_TIMEOUT and clears the word, and the
+ * context stays usable.  Nothing faults, traps or hangs.
+ */
+int bcfmm_debug_expire_wait(bcfmm_ctx* ctx, int32_t spins);
+
 #ifdef __cplusplus
 }
 #endif

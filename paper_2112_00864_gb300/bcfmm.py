@@ -24,7 +24,7 @@ EXPORTED = ["bcfmm_default_params", "bcfmm_build_bc_tree", "bcfmm_set_density", 
             "bcfmm_eval_vtb", "bcfmm_eval_btv", "bcfmm_stats", "bcfmm_last_error", "bcfmm_destroy",
             "bcfmm_debug_m2l_matrix", "bcfmm_eval_noalloc", "bcfmm_build_batch", "bcfmm_eval_graph",
             "bcfmm_build_like", "bcfmm_direct_sample", "bcfmm_mlp_blob_size", "bcfmm_mlp_dataset",
-            "bcfmm_mlp_grad", "bcfmm_mlp_adam", "bcfmm_mlp_predict"]
+            "bcfmm_mlp_grad", "bcfmm_mlp_adam", "bcfmm_mlp_predict", "bcfmm_debug_expire_wait"]
 NEAR_MODE = {"fp64": 0, "learned": 1, "none": 2}
 TASK_BIT = {"vtv": 1, "vtb": 2, "btv": 4}
 
@@ -90,6 +90,8 @@ def load(path: str = LIB_PATH):
         L.bcfmm_mlp_adam.restype = C.c_int
         L.bcfmm_mlp_predict.argtypes = [p, p, p, i64, p, p]
         L.bcfmm_mlp_predict.restype = C.c_int
+        L.bcfmm_debug_expire_wait.argtypes = [p, i32]
+        L.bcfmm_debug_expire_wait.restype = C.c_int
         _lib = L
     return _lib
 

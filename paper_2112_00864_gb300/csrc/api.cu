@@ -1079,6 +1079,12 @@ extern "C" int bcfmm_mlp_predict(const float* params, const float* feat, const f
   return BCFMM_OK;
 }
 
+extern "C" int bcfmm_debug_expire_wait(bcfmm_ctx* C, int32_t spins) {
+  if (!C || spins < 1 || spins > (1 << 20)) return fail(BCFMM_ERR_ARG, "debug_expire_wait: null context or spins not in 1..2^20");
+  CU(launch_debug_expire_wait(C->err, spins, C->st));
+  return BCFMM_OK;
+}
+
 extern "C" int bcfmm_stats(const bcfmm_ctx* C, char* json, size_t cap) {
   if (!C || !json) return fail(BCFMM_ERR_ARG, "stats: null argument");
   std::string s = "{";

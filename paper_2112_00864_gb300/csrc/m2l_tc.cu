@@ -171,11 +171,24 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
 }
 
 // bounded wait: sets *err and returns false when the phase never completes
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err) {
-  for (long i = 0; i < kSpinLimit; ++i)
+__device__ __forceinline__ bool mbar_wait_n(uint32_t bar, uint32_t parity, int* err, long limit) {
+  for (long i = 0; i < limit; ++i)
     if (mbar_try_wait(bar, parity)) return true;
   atomicExch(err, 1);
   return false;
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err) {
+  return mbar_wait_n(bar, parity, err, kSpinLimit);
+}
+
+// Test of the expiry path: one thread waits, through the same bounded
+// wait, on an mbarrier whose single expected arrival never comes.
+__global__ void k_debug_expire_wait(int* err, long limit) {
+  __shared__ __align__(8) unsigned long long bar;
+  const uint32_t b = smem_u32(&bar);
+  mbar_init(b, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  mbar_wait_n(b, 0, err, limit);
 }
 
 // 1-D bulk copy global -> shared, completion counted on the mbarrier
@@ -694,6 +707,11 @@ cudaError_t m2l_tc_noalloc_scratch(int device, float2** ptr, size_t* elems) {
   *ptr = g_noalloc_ptr[device];
   *elems = kNoAllocPartialElems;
   return cudaSuccess;
+}
+
+cudaError_t launch_debug_expire_wait(int* err, long limit, cudaStream_t st) {
+  k_debug_expire_wait<<<1, 1, 0, st>>>(err, limit);
+  return cudaGetLastError();
 }
 
 }  // namespace bcfmm

@@ -25,6 +25,8 @@ cudaError_t m2l_tc_prepare_tables(int p, int ncode, const double* T /*[ncode][np
 cudaError_t launch_m2l_tc(const DevGeom& G, const DevTaskLists& L, const M2LTensorTables& tab, int ndp,
                           const float* mom, float* loc, float2* partial, void* momb, cudaStream_t st);
 int m2l_tc_npad(int p);
+// one bounded mbarrier wait that expires (sets *err); test of the error path
+cudaError_t launch_debug_expire_wait(int* err, long limit, cudaStream_t st);
 
 // Fixed device scratch for the unit partial sums of bcfmm_eval_noalloc
 // (float2 elements); the address is looked up once per device.

@@ -110,3 +110,20 @@ def test_batch_argument_errors_before_gpu(lib):
     rc = lib.bcfmm_build_batch(*args(vo, to, 0))
     assert rc == -1 and ctx.value is None
     assert lib.bcfmm_eval_graph(None, 1, None, None, None) == -1
+
+
+def test_learned_mode_arguments_checked_before_gpu(lib):
+    """A missing or malformed network blob and bad near-mode settings are
+    argument errors found before any device work."""
+    import ctypes as C
+    ctx = C.c_void_p()
+    v = np.eye(4, 3)
+    t = np.array([[0, 1, 2, 3]], np.int32)
+    for kw in (dict(near_mode=1), dict(near_mode=1, mlp_blob=b"\0" * 64), dict(near_mode=3),
+               dict(near_mode=1, mlp_tol=0.0, mlp_blob=b"\0" * bcfmm.mlp_blob_size()), dict(tc_unit=-1)):
+        q = bcfmm.default_params(**kw)
+        rc = lib.bcfmm_build_bc_tree(v.ctypes.data, 4, t.ctypes.data, 1, None, 0, C.byref(q), None, C.byref(ctx))
+        assert rc == -1 and ctx.value is None, kw
+    q = bcfmm.default_params(near_mode=1, mlp_blob=b"\0" * bcfmm.mlp_blob_size())
+    rc = lib.bcfmm_build_bc_tree(v.ctypes.data, 4, t.ctypes.data, 1, None, 0, C.byref(q), None, C.byref(ctx))
+    assert rc == -1 and b"header" in lib.bcfmm_last_error()
