@@ -72,6 +72,39 @@ def peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def max_over_ranks(ms: float, device="cuda") -> float:
+    """The slowest rank's step time (all ranks call it; 1 rank: unchanged)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def shard_by_work(work, world: int):
+    """Independent problems dealt to ranks, largest first to the least
+    loaded rank; returns the sorted problem indices of every rank."""
+    order = np.argsort(np.asarray(work), kind="stable")[::-1]
+    loads, parts = [0.0] * world, [[] for _ in range(world)]
+    for i in order:
+        r = int(np.argmin(loads))
+        parts[r].append(int(i))
+        loads[r] += float(work[i])
+    return [sorted(p) for p in parts]
+
+
+def broadcast_choice(obj):
+    """Rank 0's object on every rank (1 rank: unchanged)."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return obj
+    box = [obj]
+    dist.broadcast_object_list(box, src=0)
+    return box[0]
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -231,11 +264,7 @@ def run_ours(args):
     stage_times, stages = timed(step_stages, max(3, args.steps // 2), stages_too=True)
     if world > 1:
         torch.distributed.barrier()
-    ms = float(np.mean(times))
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(float(np.mean(times)))
     value = npts * world / (ms * 1e-3)
 
     # end to end through the C ABI with host buffers (pinned), copies inside
@@ -395,21 +424,33 @@ def run_batch(args):
     from paper_2112_00864_gb300.inputs import batch_meshes, densities
     import oracle as O
     build()
-    torch.cuda.set_device(0)
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     stream = torch.cuda.current_stream()
-    meshes = batch_meshes(64, seed=0)
-    F = [densities(m, "bumps", ndens=4, seed=1000 + i)[0] for i, m in enumerate(meshes)]
+    all_meshes = batch_meshes(64, seed=0)
+    all_F = [densities(m, "bumps", ndens=4, seed=1000 + i)[0] for i, m in enumerate(all_meshes)]
     picked, seen = [], set()
-    for i, m in enumerate(meshes):
+    for i, m in enumerate(all_meshes):
         key = (m.name.split("_")[0], m.info.get("h_req"))
         if key not in seen:
             seen.add(key)
             picked.append(i)
     t0 = time.perf_counter()
-    base = bcfmm.Context.from_meshes([meshes[i] for i in picked], p=4, precision="fp32", stream=stream)
-    best, trials = autotune(base, np.concatenate([F[i] for i in picked], axis=1), tol=1e-6, nsample=128, reps=3)
-    base.close()
+    best, trials = None, []
+    if rank == 0:
+        base = bcfmm.Context.from_meshes([all_meshes[i] for i in picked], p=4, precision="fp32", stream=stream)
+        best, trials = autotune(base, np.concatenate([all_F[i] for i in picked], axis=1), tol=1e-6, nsample=128,
+                                reps=3)
+        base.close()
+    best = broadcast_choice(best)
     tune_s = time.perf_counter() - t0
+    # independent meshes: each rank evaluates its share, no data-path collective
+    mine = shard_by_work([m.ntet for m in all_meshes], world)[rank]
+    meshes = [all_meshes[i] for i in mine]
+    F = [all_F[i] for i in mine]
     t0 = time.perf_counter()
     ctx = bcfmm.Context.from_meshes(meshes, stream=stream, **best)
     setup_s = time.perf_counter() - t0
@@ -424,20 +465,26 @@ def run_batch(args):
 
     for _ in range(args.warmup):
         step()
-    clocks = ClockSampler(0)
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local)
     clocks.start()
     times = _timed_steps(step, args.steps, stream, flush)
     clk = clocks.stop()
-    ms = float(np.mean(times))
+    ms = max_over_ranks(float(np.mean(times)))
     st = ctx.stats()
     ntet, ntri = ctx.ntet, ctx.ntri
     npts = (4 * ntet + 3 * ntri) * 4
+    if world > 1:
+        t = torch.tensor([npts], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t)                     # points of all ranks (after timing)
+        npts = int(t.item())
     # accuracy: O1 on sampled targets of 8 meshes
     uv = ctx.split(outs["vtv"].cpu().numpy(), "vtv")
     ub = ctx.split(outs["vtb"].cpu().numpy(), "vtb")
     errs = []
     rng = np.random.default_rng(3)
-    for i in rng.choice(len(meshes), 8, replace=False):
+    for i in rng.choice(len(meshes), min(8, len(meshes)), replace=False):
         m = meshes[i]
         for t, u, n, el in (("vtv", uv[i], m.ntet, m.tets), ("vtb", ub[i], m.ntri, m.tris)):
             idx = np.sort(rng.choice(n, 8, replace=False))
@@ -451,17 +498,23 @@ def run_batch(args):
     pt = _timed_steps(lambda: (plain.set_density(bcfmm.VOLUME, Fall), plain.eval_graph(("vtv", "vtb"), pouts)),
                       3, stream, flush)
     plain.close()
+    pms = max_over_ranks(float(np.mean(pt)))
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    if rank != 0:
+        return None
     return {
-        "metric": METRIC, "value": npts / (ms * 1e-3), "unit": "target pts/s", "n_gpus": 1, "steps": args.steps,
+        "metric": METRIC, "value": npts / (ms * 1e-3), "unit": "target pts/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 (P2P, expansions, M2L); f64 setup, near corrections, sums",
         "data": "synthetic: 64 analytic BC meshes, Gaussian-bump densities (no dataset)",
         "config": {"workload": "batch of 64 cube/ball BC meshes, h in {1/8,1/16,1/32}, 4 bump densities each",
-                   "nmesh": len(meshes), "ntet": int(ntet), "ntri": int(ntri), "ndens": 4,
+                   "nmesh": len(all_meshes), "meshes_rank0": len(meshes), "ntet_rank0": int(ntet),
+                   "ntri_rank0": int(ntri), "ndens": 4, "sharding": "meshes dealt to ranks by tet count",
                    "l2": "flushed between steps", "autotuned": best},
         "accuracy": {"rel_l2_vs_oracle_max": max(errs), "samples": len(errs), "ok": bool(max(errs) <= 1e-6)},
-        "plain_fp64": {"value": npts / (float(np.mean(pt)) * 1e-3), "ms_per_step": float(np.mean(pt)),
-                       "chosen_over_plain": float(np.mean(pt)) / ms},
+        "plain_fp64": {"value": npts / (pms * 1e-3), "ms_per_step": pms, "chosen_over_plain": pms / ms},
         "autotune": {"seconds": tune_s, "meshes": len(picked),
                      "trials": [dict(t.params, ms=t.ms, err=t.err, ok=t.ok) for t in trials]},
         "gpu_launches": int(st["graph_kernels"]) * args.steps, "clocks": clk, "setup_s": setup_s,
