@@ -192,7 +192,10 @@ int bcfmm_eval_btv(bcfmm_ctx* ctx, double* out, int32_t out_is_device);
  * by one; the graph removes the per-kernel launch overhead of the many
  * small per-level stages).  Outputs as in bcfmm_eval_*, device memory only;
  * a pointer whose bit is clear is ignored.  When VtV and VtB are both in
- * the mask, VtB reuses VtV's weights and upward pass (same density).
+ * the mask, VtB reuses VtV's weights, upward pass and local expansions (same
+ * density and source points: the same interaction lists; VtV's far field
+ * covers every box with tet or triangle points), so VtB adds only its near
+ * field, L2P and element sums.
  * The first call for a given (mask, output pointers, density counts, work
  * buffers) combination captures and instantiates the graph on a stream the
  * library owns (this allocates); later calls with the same combination

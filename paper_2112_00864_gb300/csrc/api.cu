@@ -775,9 +775,12 @@ extern "C" int bcfmm_set_density(bcfmm_ctx* C, int32_t kind, const double* vals,
   return ensure_work(C, C->ndp[kind]);
 }
 
-// skip_up: the moments and weights already hold this task's source side
-// (VtB right after VtV of the same volume density in one graph).
-static int eval_impl(bcfmm_ctx* C, int t, double* out, int out_is_device, bool skip_up = false) {
+// skip_up: the moments and weights already hold this task's source side;
+// skip_far: the local expansions already hold this task's far field (both:
+// VtB right after VtV of the same volume density in one graph, VtV's lists
+// covering every box with tet or triangle points).
+static int eval_impl(bcfmm_ctx* C, int t, double* out, int out_is_device, bool skip_up = false,
+                     bool skip_far = false) {
   if (!C) return fail(BCFMM_ERR_ARG, "eval: null context");
   TaskDev& D = C->task[t];
   const DevTaskLists& L = D.L;
@@ -804,7 +807,7 @@ static int eval_impl(bcfmm_ctx* C, int t, double* out, int out_is_device, bool s
       CU(launch_weights<double>(G, L.src_cls, nsp, C->dens[kind], nsel, ndens, ndp, C->W64, st));
       CU(cudaMemsetAsync(C->mom64, 0, nexp * sizeof(double), st));
     }
-    CU(cudaMemsetAsync(C->loc64, 0, nexp * sizeof(double), st));
+    if (!skip_far) CU(cudaMemsetAsync(C->loc64, 0, nexp * sizeof(double), st));
     if (tm) CU(cudaEventRecord(ev[1], st));
     if (!skip_up) {
       CU(launch_p2m<double>(G, L, C->W64, nsp, ndp, C->mom64, st));
@@ -814,9 +817,9 @@ static int eval_impl(bcfmm_ctx* C, int t, double* out, int out_is_device, bool s
       }
     }
     if (tm) CU(cudaEventRecord(ev[2], st));
-    CU(launch_m2l_simt<double>(G, L, C->T64, G.tri_k, ndp, C->mom64, C->loc64, st));
+    if (!skip_far) CU(launch_m2l_simt<double>(G, L, C->T64, G.tri_k, ndp, C->mom64, C->loc64, st));
     if (tm) CU(cudaEventRecord(ev[3], st));
-    for (int l = 3; l < C->nlevels; ++l) {
+    for (int l = 3; l < C->nlevels && !skip_far; ++l) {
       const int n = D.l2l_off[l + 1] - D.l2l_off[l];
       CU(launch_l2l<double>(G, D.l2l_child + D.l2l_off[l], n, C->L2L64, ndp, C->loc64, st));
     }
@@ -827,7 +830,7 @@ static int eval_impl(bcfmm_ctx* C, int t, double* out, int out_is_device, bool s
       CU(launch_weights<float>(G, L.src_cls, nsp, C->dens[kind], nsel, ndens, ndp, C->W32, st));
       CU(cudaMemsetAsync(C->mom32, 0, nexp * sizeof(float), st));
     }
-    CU(cudaMemsetAsync(C->loc32, 0, nexp * sizeof(float), st));
+    if (!skip_far) CU(cudaMemsetAsync(C->loc32, 0, nexp * sizeof(float), st));
     if (tm) CU(cudaEventRecord(ev[1], st));
     if (!skip_up) {
       CU(launch_p2m<float>(G, L, C->W32, nsp, ndp, C->mom32, st));
@@ -837,10 +840,14 @@ static int eval_impl(bcfmm_ctx* C, int t, double* out, int out_is_device, bool s
       }
     }
     if (tm) CU(cudaEventRecord(ev[2], st));
-    if (tc) CU(launch_m2l_tc(G, L, C->tc, ndp, C->mom32, C->loc32, C->tc_partial, C->tc_momb, st));
-    else CU(launch_m2l_simt<float>(G, L, C->T32, G.tri_k, ndp, C->mom32, C->loc32, st));
+    if (skip_far) {
+    } else if (tc) {
+      CU(launch_m2l_tc(G, L, C->tc, ndp, C->mom32, C->loc32, C->tc_partial, C->tc_momb, st));
+    } else {
+      CU(launch_m2l_simt<float>(G, L, C->T32, G.tri_k, ndp, C->mom32, C->loc32, st));
+    }
     if (tm) CU(cudaEventRecord(ev[3], st));
-    for (int l = 3; l < C->nlevels; ++l) {
+    for (int l = 3; l < C->nlevels && !skip_far; ++l) {
       const int n = D.l2l_off[l + 1] - D.l2l_off[l];
       CU(launch_l2l<float>(G, D.l2l_child + D.l2l_off[l], n, C->L2L32, ndp, C->loc32, st));
     }
@@ -871,8 +878,9 @@ extern "C" int bcfmm_eval_btv(bcfmm_ctx* C, double* out, int32_t d) { return eva
 // Several tasks through one CUDA graph.  The graph is captured on a
 // library-owned stream the first time a (task mask, outputs, density
 // sizes, work buffers) combination is seen, and replayed on the context's
-// stream afterwards.  VtB right after VtV reuses VtV's upward pass (same
-// volume density, same source points).
+// stream afterwards.  VtB right after VtV reuses VtV's upward pass and its
+// local expansions (same volume density and source points, so the same
+// interaction lists; VtV's far field covers the boxes of both).
 extern "C" int bcfmm_eval_graph(bcfmm_ctx* C, int32_t mask, double* out_vtv, double* out_vtb, double* out_btv) {
   if (!C) return fail(BCFMM_ERR_ARG, "eval_graph: null context");
   if (mask <= 0 || mask > 7) return fail(BCFMM_ERR_ARG, "eval_graph: task mask must be a non-empty subset of 1|2|4");
@@ -899,7 +907,7 @@ extern "C" int bcfmm_eval_graph(bcfmm_ctx* C, int32_t mask, double* out_vtv, dou
     CU(cudaStreamBeginCapture(C->cap_st, cudaStreamCaptureModeRelaxed));
     int rc = BCFMM_OK;
     for (int t = 0; t < 3 && rc == BCFMM_OK; ++t)
-      if (mask >> t & 1) rc = eval_impl(C, t, outs[t], 1, t == 1 && (mask & 1));
+      if (mask >> t & 1) rc = eval_impl(C, t, outs[t], 1, t == 1 && (mask & 1), t == 1 && (mask & 1));
     cudaGraph_t graph = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(C->cap_st, &graph);
     C->st = user;

@@ -268,6 +268,12 @@ void build_lists(HostSetup& H, double eta0) {
     int sc = T.src_cls, tc = T.tgt_cls;
     auto nsrc = [&](int b) { return H.box[b].pt1[sc] - H.box[b].pt0[sc]; };
     auto ntgt = [&](int b) { return H.box[b].pt1[tc] - H.box[b].pt0[tc]; };
+    // far-field targets: VtV's local expansions also serve VtB (same source
+    // class, so the same interaction lists): VtV covers every box with tet
+    // or triangle points, and VtB evaluated right after VtV reuses them
+    auto ftgt = [&](int b) {
+      return t == 0 ? (H.box[b].pt1[0] - H.box[b].pt0[0]) + (H.box[b].pt1[1] - H.box[b].pt0[1]) : ntgt(b);
+    };
     T.near_off.push_back(0);
     T.run_off.push_back(0);
     T.vl_off.push_back(0);
@@ -305,7 +311,7 @@ void build_lists(HostSetup& H, double eta0) {
       }
       if (B.nchild == 0 && nsrc(bi) > 0) T.p2m_leaf.push_back(bi);
       if (B.nchild > 0 && nsrc(bi) > 0) T.m2m_parent[B.level].push_back(bi);
-      if (B.level >= 2 && ntgt(bi) > 0) {
+      if (B.level >= 2 && ftgt(bi) > 0) {
         T.m2l_tgt.push_back(bi);
         for (int c : vlist[bi]) {
           if (nsrc(c) == 0) continue;
@@ -316,7 +322,7 @@ void build_lists(HostSetup& H, double eta0) {
         }
         T.vl_off.push_back((int)T.vl_src.size());
         if (B.level >= 3) T.l2l_child[B.level].push_back(bi);
-        if (B.nchild == 0) T.l2p_leaf.push_back(bi);
+        if (B.nchild == 0 && ntgt(bi) > 0) T.l2p_leaf.push_back(bi);
       }
     }
   }

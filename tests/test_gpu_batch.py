@@ -105,20 +105,30 @@ def test_graph_matches_eval(bc, small_batch):
     meshes, F, G = small_batch
     ctx = _batch_ctx(bc, meshes, F, G, p=6, leaf_size=64, precision="bf16x2")
     ref = {t: ctx.eval(t).cpu().numpy() for t in ("vtv", "vtb", "btv")}
+    size_b = np.concatenate([_sizes(m, "vtb") for m in meshes])
+
+    def check(outs, ref):
+        # VtV and BtV run the same launches as the per-task calls; VtB takes
+        # VtV's local expansions, whose tensor-core tiles sum in another
+        # FP32 order than VtB's own, so it agrees to FP32 rounding
+        for t in ("vtv", "btv"):
+            if t in ref:
+                np.testing.assert_array_equal(outs[t].cpu().numpy(), ref[t])
+        r2, rm = rel(outs["vtb"].cpu().numpy(), ref["vtb"], size_b)
+        assert r2 <= 5e-7 and rm <= 1e-6, (r2, rm)
+
     outs = None
     for _ in range(2):                              # capture, then replay
         outs = ctx.eval_graph(("vtv", "vtb", "btv"), outs)
         torch.cuda.synchronize()
-        for t in ref:
-            np.testing.assert_array_equal(outs[t].cpu().numpy(), ref[t])
+        check(outs, ref)
     # new density values, same sizes: the replayed graph reads them
     F2 = [np.flip(f, axis=0).copy() * 0.5 for f in F]
     ctx.set_density(bc.VOLUME, np.concatenate(F2, axis=1))
     ref2 = {t: ctx.eval(t).cpu().numpy() for t in ("vtv", "vtb")}
     outs = ctx.eval_graph(("vtv", "vtb", "btv"), outs)
     torch.cuda.synchronize()
-    for t in ref2:
-        np.testing.assert_array_equal(outs[t].cpu().numpy(), ref2[t])
+    check(outs, ref2)
     assert ctx.stats()["device_error"] == 0
 
 
