@@ -84,9 +84,12 @@ def _time_graph(ctx, tasks, outs, reps: int) -> float:
 
 def autotune(base: "bcfmm.Context", dens_volume, dens_boundary=None, tasks=("vtv", "vtb"), tol: float = 1e-6,
              space: dict | None = None, nsample: int = 64, reps: int = 5, seed: int = 0, safety: float = 0.5,
-             verbose: bool = False):
+             verbose: bool = False, timer=None):
     """Returns (best params dict, list of Trial).  ``base`` is any context on
-    the meshes (its near pairs are reused); densities as for set_density."""
+    the meshes (its near pairs are reused); densities as for set_density.
+    ``timer(ctx, tasks, reps) -> ms`` replaces the CUDA-event timing of the
+    graph launches (default) when given."""
+    timer = timer or (lambda c, t, r: _time_graph(c, t, None, r))
     rng = np.random.default_rng(seed)
     base.set_density(bcfmm.VOLUME, dens_volume)
     if dens_boundary is not None:
@@ -105,7 +108,7 @@ def autotune(base: "bcfmm.Context", dens_volume, dens_boundary=None, tasks=("vtv
             ctx.set_density(bcfmm.VOLUME, dens_volume)
             if dens_boundary is not None:
                 ctx.set_density(bcfmm.BOUNDARY, dens_boundary)
-            tr.ms = _time_graph(ctx, tasks, None, reps)
+            tr.ms = timer(ctx, tasks, reps)
             outs = ctx.eval_graph(tasks)
             for t in tasks:
                 idx, ref, size = refs[t]
