@@ -336,6 +336,21 @@ int bcfmm_debug_m2l_matrix(int32_t p, const double* o, double* T);
  */
 int bcfmm_debug_expire_wait(bcfmm_ctx* ctx, int32_t spins);
 
+/*
+ * Test hook, host only (no GPU, no context): builds the octree and lists of
+ * the meshes exactly as bcfmm_build_batch does (one mesh: nmesh = 1; same
+ * array conventions) and checks the FMM's covering of the interactions
+ * (Sec. 2 and Sec. 3: near field N* plus the interaction lists of a leaf
+ * and its ancestors).  out[3] (host): per task (VtV, VtB, BtV), the number
+ * of (target leaf, source point) pairs not covered exactly once, counting a
+ * source point of another mesh of a batch as one that must not be covered.
+ * 0 everywhere means every pair is evaluated once, by P2P or by one M2L.
+ * Errors: BCFMM_ERR_ARG, BCFMM_ERR_MESH.
+ */
+int bcfmm_debug_list_coverage(const double* verts, const int64_t* vert_off, const int32_t* tets,
+                              const int64_t* tet_off, const int32_t* tris, const int64_t* tri_off, int32_t nmesh,
+                              const bcfmm_params* prm, int64_t* out);
+
 #ifdef __cplusplus
 }
 #endif

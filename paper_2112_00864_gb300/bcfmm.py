@@ -24,7 +24,8 @@ EXPORTED = ["bcfmm_default_params", "bcfmm_build_bc_tree", "bcfmm_set_density", 
             "bcfmm_eval_vtb", "bcfmm_eval_btv", "bcfmm_stats", "bcfmm_last_error", "bcfmm_destroy",
             "bcfmm_debug_m2l_matrix", "bcfmm_eval_noalloc", "bcfmm_build_batch", "bcfmm_eval_graph",
             "bcfmm_build_like", "bcfmm_direct_sample", "bcfmm_mlp_blob_size", "bcfmm_mlp_dataset",
-            "bcfmm_mlp_grad", "bcfmm_mlp_adam", "bcfmm_mlp_predict", "bcfmm_debug_expire_wait"]
+            "bcfmm_mlp_grad", "bcfmm_mlp_adam", "bcfmm_mlp_predict", "bcfmm_debug_expire_wait",
+            "bcfmm_debug_list_coverage"]
 NEAR_MODE = {"fp64": 0, "learned": 1, "none": 2}
 TASK_BIT = {"vtv": 1, "vtb": 2, "btv": 4}
 
@@ -92,6 +93,8 @@ def load(path: str = LIB_PATH):
         L.bcfmm_mlp_predict.restype = C.c_int
         L.bcfmm_debug_expire_wait.argtypes = [p, i32]
         L.bcfmm_debug_expire_wait.restype = C.c_int
+        L.bcfmm_debug_list_coverage.argtypes = [p, p, p, p, p, p, i32, C.POINTER(Params), p]
+        L.bcfmm_debug_list_coverage.restype = C.c_int
         _lib = L
     return _lib
 
@@ -374,3 +377,24 @@ def mlp_adam(params, grad, m1, m2, step: int, lr: float, beta1=0.9, beta2=0.999,
 def mlp_predict(params, feat, qhat, out, stream=None):
     _check(load().bcfmm_mlp_predict(_dev(params), _dev(feat), _dev(qhat), feat.shape[0], _dev(out),
                                     _stream_handle(stream)))
+
+
+def debug_list_coverage(meshes, **kw) -> np.ndarray:
+    """Host-only check of the FMM's interaction covering for one mesh or a
+    batch: per task, the (target leaf, source point) pairs not covered
+    exactly once (see include/bcfmm.h)."""
+    vo, to, ro = [0], [0], [0]
+    for m in meshes:
+        vo.append(vo[-1] + len(m.verts))
+        to.append(to[-1] + len(m.tets))
+        ro.append(ro[-1] + len(m.tris))
+    verts = np.ascontiguousarray(np.concatenate([m.verts for m in meshes]), np.float64)
+    tets = np.ascontiguousarray(np.concatenate([m.tets for m in meshes]), np.int32)
+    tris = np.ascontiguousarray(np.concatenate([np.asarray(m.tris).reshape(-1, 3) for m in meshes]), np.int32)
+    vo, to, ro = (np.asarray(x, np.int64) for x in (vo, to, ro))
+    prm = default_params(**kw)
+    out = np.zeros(3, np.int64)
+    _check(load().bcfmm_debug_list_coverage(verts.ctypes.data, vo.ctypes.data, tets.ctypes.data, to.ctypes.data,
+                                            tris.ctypes.data, ro.ctypes.data, len(meshes), C.byref(prm),
+                                            out.ctypes.data))
+    return out

@@ -697,6 +697,78 @@ extern "C" int bcfmm_build_batch(const double* verts, const int64_t* vert_off, c
   }
 }
 
+// Host only: tree and lists as bcfmm_build_batch builds them, then for
+// every task and every target leaf the source points of its mesh covered
+// by the leaf's merged near-field runs plus the interaction lists of the
+// leaf and its ancestors; counts the (leaf, source point) pairs not covered
+// exactly once.
+extern "C" int bcfmm_debug_list_coverage(const double* verts, const int64_t* vert_off, const int32_t* tets,
+                                         const int64_t* tet_off, const int32_t* tris, const int64_t* tri_off,
+                                         int32_t nmesh, const bcfmm_params* prm_in, int64_t* out) {
+  if (!out || nmesh < 1 || !verts || !vert_off || !tets || !tet_off || !tri_off)
+    return fail(BCFMM_ERR_ARG, "debug_list_coverage: null argument");
+  bcfmm_params prm;
+  bcfmm_default_params(&prm);
+  if (prm_in) prm = *prm_in;
+  if (prm.leaf_size < 1 || prm.leaf_size > 128 || !(prm.eta0 >= 0.3 && prm.eta0 <= 1.0))
+    return fail(BCFMM_ERR_ARG, "debug_list_coverage: bad leaf_size or eta0");
+  try {
+    std::vector<HostSetup> parts(nmesh);
+    for (int m = 0; m < nmesh; ++m) {
+      bool me = false;
+      const int64_t nt = tet_off[m + 1] - tet_off[m], nf = tri_off[m + 1] - tri_off[m];
+      const std::string e = build_host_mesh(parts[m], verts + 3 * vert_off[m], vert_off[m + 1] - vert_off[m],
+                                            tets + 4 * tet_off[m], nt, nf > 0 ? tris + 3 * tri_off[m] : nullptr, nf,
+                                            prm, false, &me);
+      if (!e.empty()) return fail(me ? BCFMM_ERR_MESH : BCFMM_ERR_ARG, "debug_list_coverage: " + e);
+    }
+    HostSetup H;
+    if (nmesh == 1) {
+      H = std::move(parts[0]);
+      H.mesh_tet_off = {0, tet_off[1]};
+      H.mesh_tri_off = {0, tri_off[1]};
+    } else {
+      merge_setups(parts, H);
+    }
+    for (int t = 0; t < 3; ++t) {
+      const HostTask& T = H.task[t];
+      const int sc = T.src_cls, tc = T.tgt_cls;
+      const int64_t nsrc = (int64_t)H.perm[sc].size();
+      std::vector<int> k_of(H.box.size(), -1);
+      for (size_t k = 0; k < T.m2l_tgt.size(); ++k) k_of[T.m2l_tgt[k]] = (int)k;
+      const std::vector<int64_t>& toff = tc == 0 ? H.mesh_tet_off : H.mesh_tri_off;
+      const std::vector<int64_t>& soff = sc == 0 ? H.mesh_tet_off : H.mesh_tri_off;
+      const int nqt = tc == 0 ? 4 : 3, nqs = sc == 0 ? 4 : 3;
+      std::vector<int> cnt(nsrc);
+      int64_t bad = 0;
+      for (size_t i = 0; i < T.p2p_leaf.size(); ++i) {
+        const int b = T.p2p_leaf[i];
+        std::fill(cnt.begin(), cnt.end(), 0);
+        for (int r = T.run_off[i]; r < T.run_off[i + 1]; ++r)
+          for (int q = T.runs[2 * r]; q < T.runs[2 * r + 1]; ++q) cnt[q]++;
+        for (int a = b; a >= 0; a = H.box[a].parent) {
+          if (H.box[a].level < 2) continue;
+          const int k = k_of[a];
+          if (k < 0) { bad += nsrc; continue; }          // a target's ancestor without a far field
+          for (int e = T.vl_off[k]; e < T.vl_off[k + 1]; ++e) {
+            const HostBox& C = H.box[T.vl_src[e]];
+            for (int q = C.pt0[sc]; q < C.pt1[sc]; ++q) cnt[q]++;
+          }
+        }
+        // the leaf's mesh: from its first target point's element
+        const int64_t el = H.perm[tc][H.box[b].pt0[tc]] / nqt;
+        const int m = (int)(std::upper_bound(toff.begin(), toff.end(), el) - toff.begin()) - 1;
+        const int64_t s0 = nqs * soff[m], s1 = nqs * soff[m + 1];
+        for (int64_t q = 0; q < nsrc; ++q) bad += (cnt[q] != ((q >= s0 && q < s1) ? 1 : 0));
+      }
+      out[t] = bad;
+    }
+  } catch (const std::exception& ex) {
+    return fail(BCFMM_ERR_ARG, std::string("debug_list_coverage: ") + ex.what());
+  }
+  return BCFMM_OK;
+}
+
 extern "C" int bcfmm_build_like(const bcfmm_ctx* base, const bcfmm_params* prm, bcfmm_ctx** out) {
   if (out) *out = nullptr;
   if (!base || !prm || !out) return fail(BCFMM_ERR_ARG, "build_like: null argument");

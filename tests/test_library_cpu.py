@@ -127,3 +127,16 @@ def test_learned_mode_arguments_checked_before_gpu(lib):
     q = bcfmm.default_params(near_mode=1, mlp_blob=b"\0" * bcfmm.mlp_blob_size())
     rc = lib.bcfmm_build_bc_tree(v.ctypes.data, 4, t.ctypes.data, 1, None, 0, C.byref(q), None, C.byref(ctx))
     assert rc == -1 and b"header" in lib.bcfmm_last_error()
+
+
+@pytest.mark.parametrize("leaf_size,eta0", [(64, 0.5), (8, 0.9), (32, 0.5), (3, 0.7)])
+def test_interactions_covered_exactly_once(lib, leaf_size, eta0):
+    """Every (target leaf, source point) pair of a mesh is evaluated once:
+    by the leaf's near field N* or by one interaction list of the leaf or an
+    ancestor (Sec. 2, Sec. 3); in a batch, never across meshes.  Host-only
+    check of the library's own tree and lists (no GPU)."""
+    from paper_2112_00864_gb300.inputs import ball_bc_mesh, batch_meshes, cube_bc_mesh
+    kw = dict(leaf_size=leaf_size, eta0=eta0)
+    assert list(bcfmm.debug_list_coverage([cube_bc_mesh(0.25, 0.125)], **kw)) == [0, 0, 0]
+    assert list(bcfmm.debug_list_coverage([ball_bc_mesh(2, radial=0.35)], **kw)) == [0, 0, 0]
+    assert list(bcfmm.debug_list_coverage(batch_meshes(4, seed=3, hs=(1 / 4, 1 / 8)), **kw)) == [0, 0, 0]
