@@ -341,10 +341,13 @@ int bcfmm_debug_expire_wait(bcfmm_ctx* ctx, int32_t spins);
  * the meshes exactly as bcfmm_build_batch does (one mesh: nmesh = 1; same
  * array conventions) and checks the FMM's covering of the interactions
  * (Sec. 2 and Sec. 3: near field N* plus the interaction lists of a leaf
- * and its ancestors).  out[3] (host): per task (VtV, VtB, BtV), the number
- * of (target leaf, source point) pairs not covered exactly once, counting a
- * source point of another mesh of a batch as one that must not be covered.
- * 0 everywhere means every pair is evaluated once, by P2P or by one M2L.
+ * and its ancestors).  out[6] (host): out[0..2], per task (VtV, VtB, BtV),
+ * the number of (target leaf, source point) pairs not covered exactly once,
+ * counting a source point of another mesh of a batch as one that must not
+ * be covered (0: every pair is evaluated once, by P2P or by one M2L);
+ * out[3..5], per task, the interaction-list entries that the tensor-core
+ * tiles (128 target rows, one source box per row and offset) miss,
+ * duplicate or invent (0: the tiles reproduce every list exactly).
  * Errors: BCFMM_ERR_ARG, BCFMM_ERR_MESH.
  */
 int bcfmm_debug_list_coverage(const double* verts, const int64_t* vert_off, const int32_t* tets,

@@ -381,8 +381,9 @@ def mlp_predict(params, feat, qhat, out, stream=None):
 
 def debug_list_coverage(meshes, **kw) -> np.ndarray:
     """Host-only check of the FMM's interaction covering for one mesh or a
-    batch: per task, the (target leaf, source point) pairs not covered
-    exactly once (see include/bcfmm.h)."""
+    batch: [0:3] per task the (target leaf, source point) pairs not covered
+    exactly once, [3:6] per task the interaction entries the tensor-core
+    tiles get wrong (see include/bcfmm.h)."""
     vo, to, ro = [0], [0], [0]
     for m in meshes:
         vo.append(vo[-1] + len(m.verts))
@@ -393,7 +394,7 @@ def debug_list_coverage(meshes, **kw) -> np.ndarray:
     tris = np.ascontiguousarray(np.concatenate([np.asarray(m.tris).reshape(-1, 3) for m in meshes]), np.int32)
     vo, to, ro = (np.asarray(x, np.int64) for x in (vo, to, ro))
     prm = default_params(**kw)
-    out = np.zeros(3, np.int64)
+    out = np.zeros(6, np.int64)
     _check(load().bcfmm_debug_list_coverage(verts.ctypes.data, vo.ctypes.data, tets.ctypes.data, to.ctypes.data,
                                             tris.ctypes.data, ro.ctypes.data, len(meshes), C.byref(prm),
                                             out.ctypes.data))

@@ -763,6 +763,35 @@ extern "C" int bcfmm_debug_list_coverage(const double* verts, const int64_t* ver
       }
       out[t] = bad;
     }
+    // tensor-core tiles: the (offset code, source box) entries of each row
+    // must be exactly the row's interaction list
+    for (int t = 0; t < 3; ++t) {
+      build_tc_tiles(H, t, 128);
+      const HostTask& T = H.task[t];
+      std::vector<int> k_of(H.box.size(), -1);
+      for (size_t k = 0; k < T.m2l_tgt.size(); ++k) k_of[T.m2l_tgt[k]] = (int)k;
+      std::vector<std::vector<std::pair<int, int>>> seen(T.m2l_tgt.size());
+      int64_t bad = 0;
+      const int ntile = (int)T.tc_tile_off.size() - 1;
+      for (int tl = 0; tl < ntile; ++tl)
+        for (int r = 0; r < 128; ++r) {
+          const int tgt = T.tc_tile_tgt[(size_t)tl * 128 + r];
+          for (int e = T.tc_tile_off[tl]; e < T.tc_tile_off[tl + 1]; ++e) {
+            const int src = T.tc_ent_src[(size_t)e * 128 + r];
+            if (src < 0) continue;
+            if (tgt < 0 || k_of[tgt] < 0) { ++bad; continue; }
+            seen[k_of[tgt]].push_back({T.tc_ent_code[e], src});
+          }
+        }
+      for (size_t k = 0; k < T.m2l_tgt.size(); ++k) {
+        std::vector<std::pair<int, int>> want;
+        for (int e = T.vl_off[k]; e < T.vl_off[k + 1]; ++e) want.push_back({T.vl_code[e], T.vl_src[e]});
+        std::sort(want.begin(), want.end());
+        std::sort(seen[k].begin(), seen[k].end());
+        if (want != seen[k]) bad += (int64_t)std::max(want.size(), seen[k].size());
+      }
+      out[3 + t] = bad;
+    }
   } catch (const std::exception& ex) {
     return fail(BCFMM_ERR_ARG, std::string("debug_list_coverage: ") + ex.what());
   }
