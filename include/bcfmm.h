@@ -350,6 +350,20 @@ int bcfmm_debug_expire_wait(bcfmm_ctx* ctx, int32_t spins);
  * duplicate or invent (0: the tiles reproduce every list exactly).
  * Errors: BCFMM_ERR_ARG, BCFMM_ERR_MESH.
  */
+/*
+ * Test hook, host only (no GPU, no context): the near element pairs the
+ * build finds for one mesh and task (eta(t,s) > eta_ns, Eq. def:sepRatio
+ * with centroids and largest vertex distances), as a CSR over target
+ * elements with ascending source indices.
+ *   row_off  host int64 [ntarget + 1] (ntet for VtV/BtV, ntri for VtB)
+ *   cols     host int32 [cap]; *nnz receives the pair count
+ * Errors: BCFMM_ERR_ARG (also when cap < pair count: *nnz and row_off are
+ * filled, cols is not), BCFMM_ERR_MESH.
+ */
+int bcfmm_debug_near_pairs(const double* verts, int64_t nvert, const int32_t* tets, int64_t ntet,
+                           const int32_t* tris, int64_t ntri, double eta_ns, int32_t task, int64_t cap,
+                           int64_t* row_off, int32_t* cols, int64_t* nnz);
+
 int bcfmm_debug_list_coverage(const double* verts, const int64_t* vert_off, const int32_t* tets,
                               const int64_t* tet_off, const int32_t* tris, const int64_t* tri_off, int32_t nmesh,
                               const bcfmm_params* prm, int64_t* out);

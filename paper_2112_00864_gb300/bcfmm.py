@@ -25,7 +25,7 @@ EXPORTED = ["bcfmm_default_params", "bcfmm_build_bc_tree", "bcfmm_set_density", 
             "bcfmm_debug_m2l_matrix", "bcfmm_eval_noalloc", "bcfmm_build_batch", "bcfmm_eval_graph",
             "bcfmm_build_like", "bcfmm_direct_sample", "bcfmm_mlp_blob_size", "bcfmm_mlp_dataset",
             "bcfmm_mlp_grad", "bcfmm_mlp_adam", "bcfmm_mlp_predict", "bcfmm_debug_expire_wait",
-            "bcfmm_debug_list_coverage"]
+            "bcfmm_debug_list_coverage", "bcfmm_debug_near_pairs"]
 NEAR_MODE = {"fp64": 0, "learned": 1, "none": 2}
 TASK_BIT = {"vtv": 1, "vtb": 2, "btv": 4}
 
@@ -95,6 +95,8 @@ def load(path: str = LIB_PATH):
         L.bcfmm_debug_expire_wait.restype = C.c_int
         L.bcfmm_debug_list_coverage.argtypes = [p, p, p, p, p, p, i32, C.POINTER(Params), p]
         L.bcfmm_debug_list_coverage.restype = C.c_int
+        L.bcfmm_debug_near_pairs.argtypes = [p, i64, p, i64, p, i64, d, i32, i64, p, p, C.POINTER(C.c_int64)]
+        L.bcfmm_debug_near_pairs.restype = C.c_int
         _lib = L
     return _lib
 
@@ -399,3 +401,22 @@ def debug_list_coverage(meshes, **kw) -> np.ndarray:
                                             tris.ctypes.data, ro.ctypes.data, len(meshes), C.byref(prm),
                                             out.ctypes.data))
     return out
+
+
+def debug_near_pairs(mesh, task: str, eta_ns: float | None = None):
+    """Host-only: the near pairs the build finds, (row_off, cols) CSR."""
+    t = {"vtv": 0, "vtb": 1, "btv": 2}[task]
+    v = np.ascontiguousarray(mesh.verts, np.float64)
+    te = np.ascontiguousarray(mesh.tets, np.int32)
+    tr = np.ascontiguousarray(np.asarray(mesh.tris).reshape(-1, 3), np.int32)
+    nrow = (len(tr) if t == 1 else len(te)) + 1
+    row = np.zeros(nrow, np.int64)
+    nnz = C.c_int64()
+    eta = default_params().eta_ns if eta_ns is None else eta_ns
+    L = load()
+    L.bcfmm_debug_near_pairs(v.ctypes.data, len(v), te.ctypes.data, len(te), tr.ctypes.data, len(tr), eta, t, 0,
+                             row.ctypes.data, None, C.byref(nnz))
+    cols = np.zeros(max(1, nnz.value), np.int32)
+    _check(L.bcfmm_debug_near_pairs(v.ctypes.data, len(v), te.ctypes.data, len(te), tr.ctypes.data, len(tr), eta, t,
+                                    len(cols), row.ctypes.data, cols.ctypes.data, C.byref(nnz)))
+    return row, cols[:nnz.value]

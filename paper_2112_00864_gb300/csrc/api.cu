@@ -697,6 +697,35 @@ extern "C" int bcfmm_build_batch(const double* verts, const int64_t* vert_off, c
   }
 }
 
+// Host only: the near element pairs of one mesh and task as the build
+// finds them (CSR over target elements, sorted source indices).
+extern "C" int bcfmm_debug_near_pairs(const double* verts, int64_t nvert, const int32_t* tets, int64_t ntet,
+                                      const int32_t* tris, int64_t ntri, double eta_ns, int32_t task, int64_t cap,
+                                      int64_t* row_off, int32_t* cols, int64_t* nnz) {
+  if (!verts || !tets || !row_off || !nnz || (cap > 0 && !cols) || task < 0 || task > 2 || !(eta_ns > 0))
+    return fail(BCFMM_ERR_ARG, "debug_near_pairs: bad argument");
+  try {
+    HostSetup H;
+    bool me = false;
+    const std::string e = setup_mesh(H, verts, nvert, tets, ntet, tris, ntri, &me);
+    if (!e.empty()) return fail(me ? BCFMM_ERR_MESH : BCFMM_ERR_ARG, "debug_near_pairs: " + e);
+    bcfmm_params prm;
+    bcfmm_default_params(&prm);
+    build_tree(H, prm.leaf_size);
+    build_lists(H, prm.eta0);
+    find_near_pairs(H, eta_ns);
+    const HostTask& T = H.task[task];
+    *nnz = (int64_t)T.cor_col.size();
+    std::copy(T.cor_off.begin(), T.cor_off.end(), row_off);
+    if ((int64_t)T.cor_col.size() > cap)
+      return fail(BCFMM_ERR_ARG, "debug_near_pairs: cap too small, need " + std::to_string(T.cor_col.size()));
+    std::copy(T.cor_col.begin(), T.cor_col.end(), cols);
+  } catch (const std::exception& ex) {
+    return fail(BCFMM_ERR_ARG, std::string("debug_near_pairs: ") + ex.what());
+  }
+  return BCFMM_OK;
+}
+
 // Host only: tree and lists as bcfmm_build_batch builds them, then for
 // every task and every target leaf the source points of its mesh covered
 // by the leaf's merged near-field runs plus the interaction lists of the

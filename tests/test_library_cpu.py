@@ -141,3 +141,20 @@ def test_interactions_covered_exactly_once(lib, leaf_size, eta0):
     assert list(bcfmm.debug_list_coverage([cube_bc_mesh(0.25, 0.125)], **kw)) == [0] * 6
     assert list(bcfmm.debug_list_coverage([ball_bc_mesh(2, radial=0.35)], **kw)) == [0] * 6
     assert list(bcfmm.debug_list_coverage(batch_meshes(4, seed=3, hs=(1 / 4, 1 / 8)), **kw)) == [0] * 6
+
+
+def test_near_pairs_equal_brute_force(lib):
+    """The build's near-pair search (multi-level hash grids, both size
+    orders) finds exactly the pairs the oracle's near predicate selects when
+    every element pair is tried (Eq. def:sepRatio with centroids)."""
+    import oracle as O
+    from paper_2112_00864_gb300.inputs import ball_bc_mesh, cube_bc_mesh
+    for m, tasks in ((cube_bc_mesh(0.5, 0.25), ("vtv", "vtb", "btv")), (ball_bc_mesh(1, radial=0.5), ("vtb", "btv"))):
+        for task in tasks:
+            row, cols = bcfmm.debug_near_pairs(m, task)
+            tv = m.verts[m.tris] if task == "vtb" else m.verts[m.tets]
+            sv = m.verts[m.tris] if task == "btv" else m.verts[m.tets]
+            found = {(i, int(c)) for i in range(len(tv)) for c in cols[row[i]:row[i + 1]]}
+            brute = {(i, j) for i in range(len(tv)) for j in range(len(sv)) if O.is_near(tv[i], sv[j])}
+            assert found == brute, (m.name, task, len(found ^ brute))
+            assert all(np.all(np.diff(cols[row[i]:row[i + 1]]) > 0) for i in range(len(tv)))   # sorted, unique
