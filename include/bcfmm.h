@@ -325,6 +325,18 @@ void bcfmm_destroy(bcfmm_ctx* ctx);
 int bcfmm_debug_m2l_matrix(int32_t p, const double* o, double* T);
 
 /*
+ * Test hook: the box-scaled shift of Sec. 3.3 between a parent box and its
+ * child in octant `octant` (bit 0 x, bit 1 y, bit 2 z set: the child lies on
+ * the + side; child centre = parent centre +- s/4, child side s/2).
+ *   kind 0 (M2M): mhat_parent[b] += sum_g out[b][g] mhat_child[g]
+ *   kind 1 (L2L): lhat_child[a]  += sum_b out[a][b] lhat_parent[b]
+ * with moments scaled by s^-|beta| and locals by s^|alpha| (s the box's
+ * own side), multi-indices ordered as for bcfmm_debug_m2l_matrix.
+ * out: host [np][np].  Errors: BCFMM_ERR_ARG.
+ */
+int bcfmm_debug_shift_matrix(int32_t kind, int32_t p, int32_t octant, double* out);
+
+/*
  * Test hook for the failure path of the bounded device waits (the paper has
  * no counterpart): enqueues on the context's stream one thread that waits,
  * through the same bounded mbarrier wait the tensor-core M2L uses, on a

@@ -25,7 +25,7 @@ EXPORTED = ["bcfmm_default_params", "bcfmm_build_bc_tree", "bcfmm_set_density", 
             "bcfmm_debug_m2l_matrix", "bcfmm_eval_noalloc", "bcfmm_build_batch", "bcfmm_eval_graph",
             "bcfmm_build_like", "bcfmm_direct_sample", "bcfmm_mlp_blob_size", "bcfmm_mlp_dataset",
             "bcfmm_mlp_grad", "bcfmm_mlp_adam", "bcfmm_mlp_predict", "bcfmm_debug_expire_wait",
-            "bcfmm_debug_list_coverage", "bcfmm_debug_near_pairs"]
+            "bcfmm_debug_list_coverage", "bcfmm_debug_near_pairs", "bcfmm_debug_shift_matrix"]
 NEAR_MODE = {"fp64": 0, "learned": 1, "none": 2}
 TASK_BIT = {"vtv": 1, "vtb": 2, "btv": 4}
 
@@ -97,6 +97,8 @@ def load(path: str = LIB_PATH):
         L.bcfmm_debug_list_coverage.restype = C.c_int
         L.bcfmm_debug_near_pairs.argtypes = [p, i64, p, i64, p, i64, d, i32, i64, p, p, C.POINTER(C.c_int64)]
         L.bcfmm_debug_near_pairs.restype = C.c_int
+        L.bcfmm_debug_shift_matrix.argtypes = [i32, i32, i32, p]
+        L.bcfmm_debug_shift_matrix.restype = C.c_int
         _lib = L
     return _lib
 
@@ -137,6 +139,13 @@ def debug_m2l_matrix(p: int, o) -> np.ndarray:
     o = np.ascontiguousarray(o, np.float64)
     T = np.zeros((nterms(p), nterms(p)))
     _check(load().bcfmm_debug_m2l_matrix(p, o.ctypes.data, T.ctypes.data))
+    return T
+
+
+def debug_shift_matrix(kind: str, p: int, octant: int) -> np.ndarray:
+    """Box-scaled M2M ("m2m") or L2L ("l2l") matrix for a child octant."""
+    T = np.zeros((nterms(p), nterms(p)))
+    _check(load().bcfmm_debug_shift_matrix({"m2m": 0, "l2l": 1}[kind], p, octant, T.ctypes.data))
     return T
 
 

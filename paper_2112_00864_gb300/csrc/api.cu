@@ -168,6 +168,16 @@ extern "C" void bcfmm_default_params(bcfmm_params* prm) {
 
 extern "C" const char* bcfmm_last_error(void) { return g_err.c_str(); }
 
+extern "C" int bcfmm_debug_shift_matrix(int32_t kind, int32_t p, int32_t octant, double* out) {
+  if ((kind != 0 && kind != 1) || p < 0 || p > kMaxP || octant < 0 || octant > 7 || !out)
+    return fail(BCFMM_ERR_ARG, "debug_shift_matrix: bad argument");
+  std::vector<double> Mm;
+  if (kind == 0) m2m_matrices(p, Mm); else l2l_matrices(p, Mm);
+  const size_t n = (size_t)nterms(p);
+  std::copy(Mm.begin() + octant * n * n, Mm.begin() + (octant + 1) * n * n, out);
+  return BCFMM_OK;
+}
+
 extern "C" int bcfmm_debug_m2l_matrix(int32_t p, const double* o, double* T) {
   if (p < 0 || p > kMaxP || !o || !T) return fail(BCFMM_ERR_ARG, "debug_m2l_matrix: bad argument");
   m2l_matrix_scaled(p, o, T);

@@ -158,3 +158,27 @@ def test_near_pairs_equal_brute_force(lib):
             brute = {(i, j) for i in range(len(tv)) for j in range(len(sv)) if O.is_near(tv[i], sv[j])}
             assert found == brute, (m.name, task, len(found ^ brute))
             assert all(np.all(np.diff(cols[row[i]:row[i + 1]]) > 0) for i in range(len(tv)))   # sorted, unique
+
+
+def test_shift_tables_match_oracle(lib):
+    """The library's box-scaled M2M / L2L tables reproduce the oracle's
+    unscaled shifts (Sec. 3.3) for every child octant once the box scalings
+    (moments by s^-|beta|, locals by s^|alpha|, child side s/2) are applied."""
+    import oracle as O
+    rng = np.random.default_rng(5)
+    for p in (0, 3, 6):
+        deg = O.multi_indices(p).sum(1)
+        sp = 0.8
+        cp = np.array([0.3, -0.2, 0.5])
+        for q in range(8):
+            sg = np.array([0.25 if q >> ax & 1 else -0.25 for ax in range(3)])
+            cc = cp + sg * sp
+            sc = sp / 2
+            mc = rng.standard_normal(len(deg))                 # unscaled child moments
+            ref = O.m2m(mc, cc, cp, p) / sp ** deg
+            got = bcfmm.debug_shift_matrix("m2m", p, q) @ (mc / sc ** deg)
+            assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max(), (p, q)
+            lp = rng.standard_normal(len(deg))                 # unscaled parent locals
+            ref = O.l2l(lp, cp, cc, p) * sc ** deg
+            got = bcfmm.debug_shift_matrix("l2l", p, q) @ (lp * sp ** deg)
+            assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max(), (p, q)
