@@ -363,6 +363,18 @@ int bcfmm_debug_expire_wait(bcfmm_ctx* ctx, int32_t spins);
  * Errors: BCFMM_ERR_ARG, BCFMM_ERR_MESH.
  */
 /*
+ * Test hook, host only (no GPU, no context): boxes and leaves per level of
+ * the octree the build makes for one mesh with the given leaf size (root =
+ * bounding cube of the vertices; a box holding more than leaf_size points
+ * of both classes is split; a point goes to the upper child where its
+ * coordinate is >= the box centre).  boxes, leaves: host int64 [nlev_cap].
+ * Errors: BCFMM_ERR_ARG (also when the tree is deeper than nlev_cap).
+ */
+int bcfmm_debug_tree_counts(const double* verts, int64_t nvert, const int32_t* tets, int64_t ntet,
+                            const int32_t* tris, int64_t ntri, int32_t leaf_size, int64_t* boxes, int64_t* leaves,
+                            int32_t nlev_cap);
+
+/*
  * Test hook, host only (no GPU, no context): the near element pairs the
  * build finds for one mesh and task (eta(t,s) > eta_ns, Eq. def:sepRatio
  * with centroids and largest vertex distances), as a CSR over target

@@ -25,7 +25,8 @@ EXPORTED = ["bcfmm_default_params", "bcfmm_build_bc_tree", "bcfmm_set_density", 
             "bcfmm_debug_m2l_matrix", "bcfmm_eval_noalloc", "bcfmm_build_batch", "bcfmm_eval_graph",
             "bcfmm_build_like", "bcfmm_direct_sample", "bcfmm_mlp_blob_size", "bcfmm_mlp_dataset",
             "bcfmm_mlp_grad", "bcfmm_mlp_adam", "bcfmm_mlp_predict", "bcfmm_debug_expire_wait",
-            "bcfmm_debug_list_coverage", "bcfmm_debug_near_pairs", "bcfmm_debug_shift_matrix"]
+            "bcfmm_debug_list_coverage", "bcfmm_debug_near_pairs", "bcfmm_debug_shift_matrix",
+            "bcfmm_debug_tree_counts"]
 NEAR_MODE = {"fp64": 0, "learned": 1, "none": 2}
 TASK_BIT = {"vtv": 1, "vtb": 2, "btv": 4}
 
@@ -99,6 +100,8 @@ def load(path: str = LIB_PATH):
         L.bcfmm_debug_near_pairs.restype = C.c_int
         L.bcfmm_debug_shift_matrix.argtypes = [i32, i32, i32, p]
         L.bcfmm_debug_shift_matrix.restype = C.c_int
+        L.bcfmm_debug_tree_counts.argtypes = [p, i64, p, i64, p, i64, i32, p, p, i32]
+        L.bcfmm_debug_tree_counts.restype = C.c_int
         _lib = L
     return _lib
 
@@ -429,3 +432,15 @@ def debug_near_pairs(mesh, task: str, eta_ns: float | None = None):
     _check(L.bcfmm_debug_near_pairs(v.ctypes.data, len(v), te.ctypes.data, len(te), tr.ctypes.data, len(tr), eta, t,
                                     len(cols), row.ctypes.data, cols.ctypes.data, C.byref(nnz)))
     return row, cols[:nnz.value]
+
+
+def debug_tree_counts(mesh, leaf_size: int = 64):
+    """Host-only: (boxes per level, leaves per level) of the build's octree."""
+    v = np.ascontiguousarray(mesh.verts, np.float64)
+    te = np.ascontiguousarray(mesh.tets, np.int32)
+    tr = np.ascontiguousarray(np.asarray(mesh.tris).reshape(-1, 3), np.int32)
+    b = np.zeros(24, np.int64)
+    lf = np.zeros(24, np.int64)
+    _check(load().bcfmm_debug_tree_counts(v.ctypes.data, len(v), te.ctypes.data, len(te), tr.ctypes.data, len(tr),
+                                          leaf_size, b.ctypes.data, lf.ctypes.data, len(b)))
+    return b, lf

@@ -707,6 +707,31 @@ extern "C" int bcfmm_build_batch(const double* verts, const int64_t* vert_off, c
   }
 }
 
+// Host only: boxes and leaves per level of one mesh's octree.
+extern "C" int bcfmm_debug_tree_counts(const double* verts, int64_t nvert, const int32_t* tets, int64_t ntet,
+                                       const int32_t* tris, int64_t ntri, int32_t leaf_size, int64_t* boxes,
+                                       int64_t* leaves, int32_t nlev_cap) {
+  if (!verts || !tets || !boxes || !leaves || leaf_size < 1 || leaf_size > 128 || nlev_cap < 1)
+    return fail(BCFMM_ERR_ARG, "debug_tree_counts: bad argument");
+  try {
+    HostSetup H;
+    bool me = false;
+    const std::string e = setup_mesh(H, verts, nvert, tets, ntet, tris, ntri, &me);
+    if (!e.empty()) return fail(me ? BCFMM_ERR_MESH : BCFMM_ERR_ARG, "debug_tree_counts: " + e);
+    build_tree(H, leaf_size);
+    if (H.nlevels > nlev_cap) return fail(BCFMM_ERR_ARG, "debug_tree_counts: more levels than nlev_cap");
+    std::fill(boxes, boxes + nlev_cap, 0);
+    std::fill(leaves, leaves + nlev_cap, 0);
+    for (const HostBox& B : H.box) {
+      boxes[B.level]++;
+      if (!B.nchild) leaves[B.level]++;
+    }
+  } catch (const std::exception& ex) {
+    return fail(BCFMM_ERR_ARG, std::string("debug_tree_counts: ") + ex.what());
+  }
+  return BCFMM_OK;
+}
+
 // Host only: the near element pairs of one mesh and task as the build
 // finds them (CSR over target elements, sorted source indices).
 extern "C" int bcfmm_debug_near_pairs(const double* verts, int64_t nvert, const int32_t* tets, int64_t ntet,

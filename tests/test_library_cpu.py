@@ -182,3 +182,18 @@ def test_shift_tables_match_oracle(lib):
             ref = O.l2l(lp, cp, cc, p) * sc ** deg
             got = bcfmm.debug_shift_matrix("l2l", p, q) @ (lp * sp ** deg)
             assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max(), (p, q)
+
+
+def test_tree_shape_equals_oracle_tree(lib):
+    """The build's octree and the oracle's independently written one have
+    the same boxes and leaves on every level (both compute points and box
+    centres with products and sums rounded as written, so a point on a box
+    plane lands on the same side)."""
+    import oracle as O
+    from paper_2112_00864_gb300.inputs import ball_bc_mesh, cube_bc_mesh
+    for m in (cube_bc_mesh(0.25, 0.125), ball_bc_mesh(2, radial=0.35), ball_bc_mesh(3, radial=0.5)):
+        for ls in (8, 32, 128):
+            b, lf = bcfmm.debug_tree_counts(m, ls)
+            n, ob, olf = O.tree_stats(m, leaf_size=ls)
+            assert np.array_equal(b[:20], ob[:20]) and np.array_equal(lf[:20], olf[:20]), (m.name, ls)
+            assert b.sum() == n
