@@ -225,9 +225,16 @@ int bcfmm_eval_graph(bcfmm_ctx* ctx, int32_t task_mask, double* out_vtv, double*
  * are the context's, sized by an earlier bcfmm_set_density (required once).
  * The first call on a device looks up that array's device address (a
  * one-time set-up, per device); make that first call before any stream
- * capture.  Every call on a device shares the array and overwrites it
- * completely, so nothing carries over between calls, and calls that overlap
- * on the GPU (different streams or contexts on one device) race on it.
+ * capture.  The address is kept for the life of the process, so a device
+ * reset (cudaDeviceReset, or a reset of the primary context) after the
+ * first call on that device is not supported.  Every call on a device
+ * shares the array and overwrites it completely, so nothing carries over
+ * between calls, and calls that overlap on the GPU (different streams or
+ * contexts on one device) race on it.
+ * The call does not synchronise: an expired bounded device wait of the
+ * tensor-core M2L shows only in bcfmm_stats ("device_error") and is
+ * returned, and cleared, by the next evaluation with host output.  The
+ * call records no stage timings.
  * Errors: BCFMM_ERR_ARG (null pointer, bad task, context not built with a
  * BF16-split precision, or a mesh whose M2L needs more scratch than the
  * array holds: the message gives both sizes), BCFMM_ERR_STATE (no earlier
@@ -349,20 +356,6 @@ int bcfmm_debug_shift_matrix(int32_t kind, int32_t p, int32_t octant, double* ou
 int bcfmm_debug_expire_wait(bcfmm_ctx* ctx, int32_t spins);
 
 /*
- * Test hook, host only (no GPU, no context): builds the octree and lists of
- * the meshes exactly as bcfmm_build_batch does (one mesh: nmesh = 1; same
- * array conventions) and checks the FMM's covering of the interactions
- * (Sec. 2 and Sec. 3: near field N* plus the interaction lists of a leaf
- * and its ancestors).  out[6] (host): out[0..2], per task (VtV, VtB, BtV),
- * the number of (target leaf, source point) pairs not covered exactly once,
- * counting a source point of another mesh of a batch as one that must not
- * be covered (0: every pair is evaluated once, by P2P or by one M2L);
- * out[3..5], per task, the interaction-list entries that the tensor-core
- * tiles (128 target rows, one source box per row and offset) miss,
- * duplicate or invent (0: the tiles reproduce every list exactly).
- * Errors: BCFMM_ERR_ARG, BCFMM_ERR_MESH.
- */
-/*
  * Test hook, host only (no GPU, no context): boxes and leaves per level of
  * the octree the build makes for one mesh with the given leaf size (root =
  * bounding cube of the vertices; a box holding more than leaf_size points
@@ -388,6 +381,20 @@ int bcfmm_debug_near_pairs(const double* verts, int64_t nvert, const int32_t* te
                            const int32_t* tris, int64_t ntri, double eta_ns, int32_t task, int64_t cap,
                            int64_t* row_off, int32_t* cols, int64_t* nnz);
 
+/*
+ * Test hook, host only (no GPU, no context): builds the octree and lists of
+ * the meshes exactly as bcfmm_build_batch does (one mesh: nmesh = 1; same
+ * array conventions) and checks the FMM's covering of the interactions
+ * (Sec. 2 and Sec. 3: near field N* plus the interaction lists of a leaf
+ * and its ancestors).  out[6] (host): out[0..2], per task (VtV, VtB, BtV),
+ * the number of (target leaf, source point) pairs not covered exactly once,
+ * counting a source point of another mesh of a batch as one that must not
+ * be covered (0: every pair is evaluated once, by P2P or by one M2L);
+ * out[3..5], per task, the interaction-list entries that the tensor-core
+ * tiles (128 target rows, one source box per row and offset) miss,
+ * duplicate or invent (0: the tiles reproduce every list exactly).
+ * Errors: BCFMM_ERR_ARG, BCFMM_ERR_MESH.
+ */
 int bcfmm_debug_list_coverage(const double* verts, const int64_t* vert_off, const int32_t* tets,
                               const int64_t* tet_off, const int32_t* tris, const int64_t* tri_off, int32_t nmesh,
                               const bcfmm_params* prm, int64_t* out);

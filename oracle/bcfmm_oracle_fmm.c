@@ -319,12 +319,25 @@ static int neighbour_offsets(double eta0, int (*off)[3], int cap) {
 /* task 0 VtV (sources/targets: tet points), 1 VtB (sources tet, targets tri),
  * 2 BtV (sources tri, targets tet).  dens: [ndens][nsrc elements].
  * targets: requested target elements; out[ndens][ntargets].
- * stats (optional, int64[8]): nbox, nleaf, maxlevel, n_m2l, n_p2p, 0,0,0. */
+ * stats (optional, int64[8]): nbox, nleaf, maxlevel, n_m2l, n_p2p, 0,0,0.
+ * qlev (optional, int[20]): expansion order q_l of level l (Sec. 3.3 uses
+ * q_l in the interaction phase; Sec. 4.3, Eq. def:q0, sets
+ * q_l = q0 + L - l).  Entries <= 0, or qlev NULL, mean p.  Moments are kept
+ * to order p (= the largest q_l) on every level, because a parent's
+ * moments of order q_{l-1} need its children's moments of that order; the
+ * interaction phase at level l keeps |alpha| + |beta| <= q_l, and the local
+ * expansion of a level-l box is truncated to |alpha| <= q_l (a parent's
+ * expansion is translated to the child and cut to the child's order). */
+static int level_order(const int *qlev, int level, int p) {
+  if (!qlev || level >= 20 || qlev[level] <= 0 || qlev[level] > p) return p;
+  return qlev[level];
+}
+
 int orc_fmm(int task, const double *tets, int64_t ntet, const double *tris, int64_t ntri,
             const double *dens, int ndens, int p, int Ls, double eta0, double eta_ns,
             const double *glx, const double *glw, int n, int k,
             const int64_t *targets, int64_t ntargets, double *out, double *out_fmm_only,
-            int nthreads, int64_t *stats) {
+            int nthreads, int64_t *stats, const int *qlev) {
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
 #endif
@@ -404,13 +417,16 @@ int orc_fmm(int task, const double *tets, int64_t ntet, const double *tris, int6
         int64_t sa, se; SRANGE(C, sa, se);
         if (sa == se) continue;
         double r[3] = { B->c[0]-C->c[0], B->c[1]-C->c[1], B->c[2]-C->c[2] };
-        orc_m2l_matrix(r, p, Tm);
+        /* order q_l of this level: T of order q (zero unless |a|+|b| <= q),
+         * applied to the first nterms(q) moments */
+        const int q = level_order(qlev, B->level, p), nq = nterms(q);
+        orc_m2l_matrix(r, q, Tm);
         for (int d = 0; d < ndens; ++d) {
           const double *mc = mom + ((size_t)Q->kids[c]*ndens + d)*np;
           double *lb = loc + ((size_t)bi*ndens + d)*np;
-          for (int a = 0; a < np; ++a) {
+          for (int a = 0; a < nq; ++a) {
             double s = 0.0;
-            for (int b = 0; b < np; ++b) s += Tm[a*np + b] * mc[b];
+            for (int b = 0; b < nq; ++b) s += Tm[a*nq + b] * mc[b];
             lb[a] += s;
           }
         }
@@ -422,8 +438,12 @@ int orc_fmm(int task, const double *tets, int64_t ntet, const double *tris, int6
   /* downward pass (parents first) */
   for (int bi = 1; bi < T.n; ++bi) {
     OBox *B = &T.box[bi]; OBox *P = &T.box[B->parent];
-    for (int d = 0; d < ndens; ++d)
-      orc_l2l(loc + ((size_t)B->parent*ndens + d)*np, P->c, B->c, p, loc + ((size_t)bi*ndens + d)*np);
+    const int nq = nterms(level_order(qlev, B->level, p));
+    for (int d = 0; d < ndens; ++d) {
+      double *lc = loc + ((size_t)bi*ndens + d)*np;
+      orc_l2l(loc + ((size_t)B->parent*ndens + d)*np, P->c, B->c, p, lc);
+      for (int a = nq; a < np; ++a) lc[a] = 0.0;      /* the child's order */
+    }
   }
   /* evaluation and near field in leaves */
   int64_t n_p2p = 0;

@@ -64,7 +64,7 @@ def lib():
             L.orc_tri_quad.argtypes = [p, i64, p, p]
             L.orc_direct.argtypes = [i, p, i64, p, i64, p, i, p, i64, d, p, p, i, i, p, i]
             L.orc_fmm.restype = i
-            L.orc_fmm.argtypes = [i, p, i64, p, i64, p, i, i, i, d, d, p, p, i, i, p, i64, p, p, i, p]
+            L.orc_fmm.argtypes = [i, p, i64, p, i64, p, i, i, i, d, d, p, p, i, i, p, i64, p, p, i, p, p]
             L.orc_taylor_b.argtypes = [p, i, p]
             L.orc_m2l_matrix.argtypes = [p, i, p]
             L.orc_p2m.argtypes = [p, p, i64, p, i, p]
@@ -176,8 +176,12 @@ def direct(task: str, mesh, dens, targets=None, eta_ns: float = ETA_NS, n: int =
 
 def fmm(task: str, mesh, dens, p: int = 4, leaf_size: int = 64, targets=None, eta0: float = ETA0,
         eta_ns: float = ETA_NS,
-        n: int = NEAR_N, k: int = NEAR_K, nthreads: int = 0, return_stats: bool = False):
-    """O2: the FP64 reference FMM; returns u[d, t] (and tree statistics)."""
+        n: int = NEAR_N, k: int = NEAR_K, nthreads: int = 0, return_stats: bool = False, p_level=None):
+    """O2: the FP64 reference FMM; returns u[d, t] (and tree statistics).
+
+    p_level: optional expansion order per octree level (index = level,
+    at most 20 entries; entries <= 0 mean p), the level-dependent orders of
+    Sec. 4.3; moments are kept to order p on every level."""
     tets, tris, tgt, src = _task_arrays(task, mesh)
     dens = _f64(np.atleast_2d(dens))
     targets = (np.arange(tgt.shape[0], dtype=np.int64) if targets is None
@@ -186,13 +190,24 @@ def fmm(task: str, mesh, dens, p: int = 4, leaf_size: int = 64, targets=None, et
     raw = np.zeros_like(out)
     st = np.zeros(8, np.int64)
     gx, gw = gauss_legendre01(n)
+    ql = None
+    if p_level is not None:
+        ql = np.zeros(20, np.int32)
+        q = np.asarray(p_level, np.int32)[:20]
+        ql[:len(q)] = q
     lib().orc_fmm(TASKS[task], _ptr(tets), tets.shape[0], _ptr(tris), tris.shape[0], _ptr(dens),
                   dens.shape[0], p, leaf_size, eta0, eta_ns, _ptr(gx), _ptr(gw), n, k, _ptr(targets),
-                  targets.size, _ptr(out), _ptr(raw), nthreads, _ptr(st))
+                  targets.size, _ptr(out), _ptr(raw), nthreads, _ptr(st), None if ql is None else _ptr(ql))
     if return_stats:
         keys = ["nbox", "nleaf", "maxlevel", "n_m2l", "n_p2p"]
         return out, dict(zip(keys, st[:5].tolist()), raw=raw)
     return out
+
+
+def paper_orders(q0: int, finest_level: int, nlevels: int = 20):
+    """Level-dependent expansion orders of Sec. 4.3 (Eq. def:q0, and Sec. 5's
+    q_l = 4 + L - l with q0 = 4): q_l = q0 + L - l for l <= L."""
+    return [q0 + finest_level - l if l <= finest_level else q0 for l in range(nlevels)]
 
 
 def tree_stats(mesh, leaf_size: int = 64):

@@ -1154,6 +1154,7 @@ extern "C" int bcfmm_eval_noalloc(bcfmm_ctx* C, int32_t task, const double* dens
   }
   CU(launch_p2p_l2p_f32(G, L, C->W32, nsp, ntp, ndp, C->loc32, C->phi, st));
   CU(launch_elem_sum(G, L, C->phi, ntp, dens_dev, 1, out_dev, st));
+  C->ev_rec[task] = false;             // no stage timings recorded by this call
   return BCFMM_OK;
 }
 

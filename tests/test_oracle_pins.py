@@ -248,6 +248,54 @@ def test_fmm_converges_to_direct_geometrically():
     assert np.linalg.norm(u2 - u1) / np.linalg.norm(u1) < 2e-6
 
 
+def test_fmm_vtb_converges_to_direct_geometrically():
+    """O2's triangle-target branch (VtB: tet sources, triangle targets,
+    Algorithm 2) against O1: the truncation error falls geometrically in p
+    (Eq. est:remain:G), so a slip in the triangle-target lists or the
+    evaluation at triangle points fails here, on the CPU."""
+    m = cube_bc_mesh(0.25, 0.25)
+    f, g = densities(m, "sine")
+    u1 = O.direct("vtb", m, f)
+    e = []
+    for p in (2, 4, 6, 8):
+        u2 = O.fmm("vtb", m, f, p=p, leaf_size=16)
+        e.append(np.linalg.norm(u2 - u1) / np.linalg.norm(u1))
+    assert e[0] > 5 * e[1] > 25 * e[2] > 125 * e[3], e
+    assert e[3] < 1e-6, e
+
+
+def test_fmm_level_orders():
+    """Level-dependent expansion orders (Sec. 4.3, Eq. def:q0; Sec. 5 uses
+    q_l = 4 + L - l).  A schedule whose every entry equals p reproduces the
+    uniform-order O2 bit for bit; with the paper's schedule the error
+    against O1 falls geometrically as q0 grows; and raising only the
+    coarse levels' orders changes the result by less than the error of the
+    finest level's order (the coarse levels carry the larger orders)."""
+    m = cube_bc_mesh(0.25, 0.25)
+    f, g = densities(m, "sine")
+    u1 = O.direct("vtv", m, f)
+    _, st = O.fmm("vtv", m, f, p=4, leaf_size=16, return_stats=True)
+    L = st["maxlevel"]
+    a = O.fmm("vtv", m, f, p=6, leaf_size=16)
+    b = O.fmm("vtv", m, f, p=6, leaf_size=16, p_level=[6] * 20)
+    assert np.array_equal(a, b)
+    e = []
+    for q0 in (1, 2, 3, 4):
+        q = O.paper_orders(q0, L)
+        u2 = O.fmm("vtv", m, f, p=max(q), leaf_size=16, p_level=q)
+        e.append(np.linalg.norm(u2 - u1) / np.linalg.norm(u1))
+    assert e[0] > 4 * e[1] > 16 * e[2] > 64 * e[3], e
+    # the finest level at order 2 carries most of the error: raising every
+    # other level to order 8 removes only part of it
+    q = [8] * 20
+    q[L] = 2
+    u3 = O.fmm("vtv", m, f, p=8, leaf_size=16, p_level=q)
+    u4 = O.fmm("vtv", m, f, p=8, leaf_size=16, p_level=[2] * 20)
+    e3 = np.linalg.norm(u3 - u1) / np.linalg.norm(u1)
+    e4 = np.linalg.norm(u4 - u1) / np.linalg.norm(u1)
+    assert e3 < e4, (e3, e4)
+
+
 def test_galerkin_symmetry_and_transpose():
     m = cube_bc_mesh(0.25, 0.25)
     rng = np.random.default_rng(5)

@@ -62,3 +62,32 @@ def test_eval_noalloc_rejects_misuse(bc):
     with pytest.raises(bc.BcfmmError) as e:
         tc.eval_noalloc("vtv", f, out)         # no set_density yet
     assert e.value.code == -6
+
+
+def test_eval_noalloc_expired_wait_shows_in_stats(bc):
+    """The entry point does not synchronise, so an expired bounded wait of
+    the tensor-core M2L is reported through the context's device error word
+    (bcfmm_stats), and the next evaluation with host output returns
+    BCFMM_ERR_TIMEOUT and clears it.  The expiry is made on purpose by the
+    library's test hook (a bounded wait on a barrier that nothing
+    completes); nothing faults or hangs."""
+    from paper_2112_00864_gb300.inputs import cube_bc_mesh, densities
+    m = cube_bc_mesh(0.5, 0.25)
+    f = densities(m, "sine")[0]
+    ctx = bc.Context.from_mesh(m, p=4, precision="bf16x2")
+    f_dev = torch.tensor(f, device="cuda")
+    ctx.set_density(bc.VOLUME, f_dev)
+    ref = ctx.eval_vtv().cpu().numpy()[0]
+    assert ctx._lib.bcfmm_debug_expire_wait(ctx._ctx, 1000) == 0
+    out = torch.empty(m.ntet, dtype=torch.float64, device="cuda")
+    ctx.eval_noalloc("vtv", f_dev[0].contiguous(), out)
+    torch.cuda.synchronize()
+    assert ctx.stats()["device_error"] == 1
+    host = np.zeros((1, m.ntet))
+    with pytest.raises(bc.BcfmmError) as e:
+        ctx.eval_vtv(host)
+    assert e.value.code == -5
+    assert ctx.stats()["device_error"] == 0
+    ctx.eval_noalloc("vtv", f_dev[0].contiguous(), out)
+    u = out.cpu().numpy()
+    assert np.linalg.norm(u - ref) / np.linalg.norm(ref) <= 1e-12
