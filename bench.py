@@ -51,9 +51,11 @@ def workload():
         return dict(WORKLOAD)
     return {"workload": f"unit ball BC mesh: icosphere level {BALL_LEVEL}, radially graded tets, f=1 (small case)",
             "mesh": f"ball_bc_mesh(level={BALL_LEVEL}, radial=0.35)"}
-CHOSEN = dict(p=6, eta0=0.5, leaf_size=128, precision="bf16x2")
-PLAIN = dict(p=6, eta0=0.5, leaf_size=128, precision="fp64")
-SAMPLE_TARGETS = 64        # per task, for the accuracy gate and the CPU baseline
+# the chosen form: BF16 hi+lo tensor-core M2L with the paper's order schedule
+# q_l = min(7, 4 + L - l) (Sec. 4.3, Eq. def:q0; Sec. 5 uses q0 = 4)
+CHOSEN = dict(p=7, q0=4, eta0=0.5, leaf_size=128, precision="fp32")
+PLAIN = dict(p=7, q0=4, eta0=0.5, leaf_size=128, precision="fp64")
+SAMPLE_TARGETS = 1024      # per task, for the accuracy gate and the CPU baseline
 
 
 def dist_env():
@@ -325,21 +327,21 @@ def run_ours(args):
         sm_clk = clk.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
         pairs = st["vtv"]["p2p_pairs"] + st["vtb"]["p2p_pairs"]
         ops_p2p = 7.0 * pairs                                        # FP32-pipe ops per pair
-        fp32_peak = 152 * 128 * pk.get("sm_max_mhz", 2070.0) * 1e6  # FP32-pipe ops/s at max clock
+        nsm = torch.cuda.get_device_properties(local).multi_processor_count
+        fp32_peak = nsm * 128 * pk.get("sm_max_mhz", 2070.0) * 1e6  # FP32-pipe ops/s at max clock
         m2l_pairs = st["vtv"]["m2l_pairs"]
-        p = st["p"]
-        m2l_flop = 2.0 * math.comb(p + 6, 6) * m2l_pairs
+        # box pairs of each order times 2 C(q+6, 6): one FMA per (a, b) with |a| + |b| <= q
+        m2l_flop = sum(2.0 * math.comb(q + 6, 6) * n for q, n in enumerate(st["vtv"]["m2l_pairs_by_order"]))
         roof_p2p = {"kernel": "k_p2p_l2p_f32x2", "bound": "alu", "achieved": ops_p2p / (p2p_ms * 1e-3) / 1e12,
                     "peak": fp32_peak / 1e12, "unit": "TFLOP/s", "traffic": None,
-                    "note": "FP32-pipe ops (7 per pair: 3 sub, 1 mul, 2 fma, 1 fma) per s vs 152 SMs x 128 lanes "
-                            "x max SM clock; the rsqrt on MUFU caps it at 7/8 of this peak",
+                    "note": f"FP32-pipe ops (7 per pair: 3 sub, 1 mul, 2 fma, 1 fma) per s vs {nsm} SMs x 128 "
+                            "lanes x max SM clock; the rsqrt on MUFU caps it at 7/8 of this peak",
                     "ms_per_step": float(p2p_ms), "pairs": int(pairs)}
         roof_p2p["frac"] = roof_p2p["achieved"] / roof_p2p["peak"]
         tc = CHOSEN["precision"].startswith("bf16")
         if tc:
-            nprod = 3 if CHOSEN["precision"] == "bf16x2" else 6
             ent = st["vtv"]["tc_entries"]
-            mma_flop = 2.0 * 128 * nprod * tc_padded_macs_per_row(p) * ent
+            mma_flop = st["vtv"]["tc_mma_flop"]
             roof_m2l = {"kernel": "k_m2l_tc", "bound": "tensor", "achieved": m2l_flop / (m2l_ms * 1e-3) / 1e12,
                         "peak": pk["bf16_tflops_sustained"], "unit": "TFLOP/s", "traffic": None,
                         "note": "algorithmic flops 2*C(p+6,6) per box pair (one product) vs measured BF16 dense "
@@ -347,17 +349,22 @@ def run_ours(args):
                         "mma_tflops": mma_flop / (m2l_ms * 1e-3) / 1e12,
                         "ms_per_step": float(m2l_ms), "pairs": int(m2l_pairs), "tile_entries": int(ent)}
         else:
-            roof_m2l = {"kernel": "k_m2l_simt", "bound": "alu", "achieved": m2l_flop / (m2l_ms * 1e-3) / 1e12,
+            roof_m2l = {"kernel": "k_m2l_taylor" if CHOSEN["precision"] == "fp32" else "k_m2l_simt", "bound": "alu",
+                        "achieved": m2l_flop / (m2l_ms * 1e-3) / 1e12,
                         "peak": 2 * fp32_peak / 1e12, "unit": "TFLOP/s", "traffic": None,
-                        "note": "algorithmic FMA flops 2*C(p+6,6) per box pair vs FP32 FMA peak",
-                        "ms_per_step": float(m2l_ms), "pairs": int(m2l_pairs)}
+                        "note": "algorithmic flops 2*C(q+6,6) per box pair of order q (one FMA per (a, b), "
+                                "|a|+|b| <= q) over the whole M2L stage (prescale, chunk sums, reduce) vs FP32 "
+                                "FMA peak (2 flops x 128 lanes x SMs x max SM clock)",
+                        "ms_per_step": float(m2l_ms), "pairs": int(m2l_pairs),
+                        "orders": st["vtv"].get("taylor_orders", [])}
         roof_m2l["frac"] = roof_m2l["achieved"] / roof_m2l["peak"]
         dominant = roof_p2p if p2p_ms >= m2l_ms else roof_m2l
         roofline = dict(dominant)
         roofline["peak_source"] = src + " (derived: unit counts x max SM clock)"
         osamp_pts = 4 * len(tv) + 3 * len(tb)
+        acc_ok = bool(max(v[0] for v in err.values()) <= 1e-6)
         result = {
-            "metric": METRIC, "value": value, "unit": "target pts/s", "n_gpus": world, "steps": args.steps,
+            "metric": METRIC, "value": value if acc_ok else None, "unit": "target pts/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 (P2P, expansions, M2L); f64 setup, near corrections, sums",
             "data": "synthetic: analytic BC mesh and density (no dataset)",
@@ -366,18 +373,20 @@ def run_ours(args):
             "accuracy": {"rel_l2_vs_oracle": {k: v[0] for k, v in err.items()},
                          "rel_max_vs_oracle": {k: v[1] for k, v in err.items()},
                          "sample_targets_per_task": SAMPLE_TARGETS,
-                         "ok": bool(max(v[0] for v in err.values()) <= 1e-6)},
+                         "ok": acc_ok},
             "plain_fp64": {"value": npts / (plain_ms * 1e-3), "ms_per_step": plain_ms,
                            "rel_l2_vs_oracle": {k: v[0] for k, v in err_plain.items()},
                            "chosen_over_plain": plain_ms / ms},
             "roofline": roofline,
+            **({} if acc_ok else {"failed": "rel L2 error above 1e-6 on the sampled targets: no throughput "
+                                            f"is reported (measured {ms:.3f} ms per step)"}),
             "stages_ms": {"vtv": [float(x) for x in sv], "vtb": [float(x) for x in sb],
                           "names": ["weights+clear", "P2M+M2M", "M2L", "L2L", "L2P+P2P", "sums+corrections"]},
             "roofline_other": roof_m2l if dominant is roof_p2p else roof_p2p,
             "cpu_baseline": {"value": osamp_pts / osec, "unit": "target pts/s", "cores": cores, "kind": "oracle",
                              "sample": f"O1 direct definition on {len(tv)} VtV + {len(tb)} VtB sampled target "
                                        f"elements of the same workload ({osec:.1f} s)"},
-            "e2e": {"value": npts / (e2e_ms * 1e-3), "unit": "target pts/s",
+            "e2e": {"value": npts / (e2e_ms * 1e-3) if acc_ok else None, "unit": "target pts/s",
                     "h2d_bytes_per_step": int(f.nbytes), "d2h_bytes_per_step": int(8 * (m.ntet + m.ntri))},
             "gpu_launches": graph_kernels * args.steps,
             "graph": {"kernel_nodes_per_step": graph_kernels,

@@ -64,13 +64,17 @@ typedef enum {
  * is FP64 in every mode. */
 typedef enum {
   BCFMM_FP64 = 0,          /* plain: every pass in FP64 on CUDA cores              */
-  BCFMM_FP32 = 1,          /* P2P, P2M/M2M/L2L/L2P and M2L in FP32 (CUDA cores)     */
+  BCFMM_FP32 = 1,          /* P2P, P2M/M2M/L2L/L2P and M2L in FP32 (CUDA cores); M2L
+                              in the Taylor-coefficient form (FP32 products, FP64
+                              sums over list chunks)                              */
   BCFMM_FP32_BF16X2 = 2,   /* FP32, M2L on tcgen05 tensor cores, BF16 hi+lo split
                               (hi*hi + hi*lo + lo*hi), FP32 accumulation in TMEM   */
   BCFMM_FP32_BF16X3 = 3    /* as above with a 3-term split (6 products)            */
 } bcfmm_precision;
 
 typedef enum { BCFMM_VOLUME = 0, BCFMM_BOUNDARY = 1 } bcfmm_density_kind;
+
+#define BCFMM_MAX_LEVELS 20   /* entries of bcfmm_params.p_level */
 
 typedef struct {
   int32_t p;            /* expansion order (total degree), 0..12; default 6            */
@@ -98,6 +102,19 @@ typedef struct {
   const void* mlp_blob; /* near_mode 1: trained network and calibration, format of
                            bcfmm_mlp_blob_size(); read during the build only           */
   int64_t mlp_blob_bytes;
+  int32_t p_level[BCFMM_MAX_LEVELS];
+                        /* expansion order of each octree level (Sec. 3.3 uses q_l in
+                           the interaction phase; Sec. 4.3, Eq. def:q0, sets
+                           q_l = q0 + L - l, Sec. 5 uses q0 = 4): the interaction
+                           phase of level l keeps |alpha| + |beta| <= q_l and a
+                           level-l local expansion has total degree <= q_l (a
+                           parent's expansion is cut to the child's order);
+                           moments are kept to order p on every level, so p must be
+                           >= every q_l.  0 = p (default: uniform order p); 0..p  */
+  int32_t q0;           /* > 0: the schedule of Sec. 4.3 (Eq. def:q0) instead of
+                           p_level: q_l = min(p, q0 + L - l), L the deepest level of
+                           the octree (over every mesh of a batch); 0 = use p_level;
+                           0..12                                                    */
 } bcfmm_params;
 
 /* Fills *prm with the defaults above.  Never fails. */
@@ -214,13 +231,14 @@ int bcfmm_eval_graph(bcfmm_ctx* ctx, int32_t task_mask, double* out_vtv, double*
  * during evaluation: a host framework that owns and budgets all device
  * memory itself, or a latency-critical loop where cudaMalloc/cudaFree could
  * synchronise the device.  The paper has no counterpart; this is a
- * deployment variant of the tensor-core interaction phase.
+ * deployment variant of the FP32 evaluation (precision BCFMM_FP32 or a
+ * BF16 split).
  *   dens_dev  FP64 device array, one P0 value per source element (tets for
  *             VtV/VtB, triangles for BtV); read on the context's stream
  *   out_dev   FP64 device array, one value per target element; written
  *             asynchronously on the context's stream
- * The tensor-core M2L keeps its per-unit partial sums in a fixed static
- * device array of 64 MiB (every GPU that loads the library holds it until
+ * The M2L keeps its partial sums (tensor cores: per work unit; Taylor
+ * form: per list chunk) in a fixed static device array of 64 MiB (every GPU that loads the library holds it until
  * the process exits) instead of the context's scratch; all other buffers
  * are the context's, sized by an earlier bcfmm_set_density (required once).
  * The first call on a device looks up that array's device address (a
@@ -235,8 +253,8 @@ int bcfmm_eval_graph(bcfmm_ctx* ctx, int32_t task_mask, double* out_vtv, double*
  * tensor-core M2L shows only in bcfmm_stats ("device_error") and is
  * returned, and cleared, by the next evaluation with host output.  The
  * call records no stage timings.
- * Errors: BCFMM_ERR_ARG (null pointer, bad task, context not built with a
- * BF16-split precision, or a mesh whose M2L needs more scratch than the
+ * Errors: BCFMM_ERR_ARG (null pointer, bad task, context built with
+ * precision BCFMM_FP64, or a mesh whose M2L needs more scratch than the
  * array holds: the message gives both sizes), BCFMM_ERR_STATE (no earlier
  * bcfmm_set_density, or the current device is not the context's),
  * BCFMM_ERR_CUDA.
@@ -332,6 +350,16 @@ void bcfmm_destroy(bcfmm_ctx* ctx);
 int bcfmm_debug_m2l_matrix(int32_t p, const double* o, double* T);
 
 /*
+ * Test hook: the per-offset coefficients of the Taylor-form M2L (precision
+ * BCFMM_FP32), g[gamma] = D^gamma G(o) for |gamma| <= q (same multi-index
+ * order), from which the kernel rebuilds the matrix above as
+ *   T[a][b] = g[a + b] (-1)^{|b|} / (a! b!),   |a| + |b| <= q.
+ * The kernel stores them in FP32.  g: host [(q+1)(q+2)(q+3)/6].
+ * Errors: BCFMM_ERR_ARG.
+ */
+int bcfmm_debug_m2l_taylor_coeffs(int32_t q, const double* o, double* g);
+
+/*
  * Test hook: the box-scaled shift of Sec. 3.3 between a parent box and its
  * child in octant `octant` (bit 0 x, bit 1 y, bit 2 z set: the child lies on
  * the + side; child centre = parent centre +- s/4, child side s/2).
@@ -386,13 +414,22 @@ int bcfmm_debug_near_pairs(const double* verts, int64_t nvert, const int32_t* te
  * the meshes exactly as bcfmm_build_batch does (one mesh: nmesh = 1; same
  * array conventions) and checks the FMM's covering of the interactions
  * (Sec. 2 and Sec. 3: near field N* plus the interaction lists of a leaf
- * and its ancestors).  out[6] (host): out[0..2], per task (VtV, VtB, BtV),
+ * and its ancestors).  out (host): out[0..2], per task (VtV, VtB, BtV),
  * the number of (target leaf, source point) pairs not covered exactly once,
  * counting a source point of another mesh of a batch as one that must not
  * be covered (0: every pair is evaluated once, by P2P or by one M2L);
  * out[3..5], per task, the interaction-list entries that the tensor-core
- * tiles (128 target rows, one source box per row and offset) miss,
- * duplicate or invent (0: the tiles reproduce every list exactly).
+ * tiles (128 target rows of one expansion order, one source box per row and
+ * offset) miss, duplicate or invent, plus rows whose order differs from the
+ * tile's (0: the tiles reproduce every list exactly); out[6..8], per task,
+ * the faults of the tensor-core schedule built for 1, 7 and 152 SMs (an
+ * entry not in exactly one unit, a unit not exactly once in one CTA's
+ * sequence, wrong first / last flags, partial slots of cut tiles not
+ * consecutive); out[9..11], per task, the faults of the Taylor-form M2L
+ * schedule built for 1, 7 and 152 SMs (a list entry of a target of order
+ * 1..7 missing, duplicated, invented or in a lane whose chunk is another
+ * target's; a chunk not in exactly one lane; a target of another order not
+ * exactly once in the generic kernel's list).  out: host int64 [12].
  * Errors: BCFMM_ERR_ARG, BCFMM_ERR_MESH.
  */
 int bcfmm_debug_list_coverage(const double* verts, const int64_t* vert_off, const int32_t* tets,

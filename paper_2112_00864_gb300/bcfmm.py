@@ -26,7 +26,7 @@ EXPORTED = ["bcfmm_default_params", "bcfmm_build_bc_tree", "bcfmm_set_density", 
             "bcfmm_build_like", "bcfmm_direct_sample", "bcfmm_mlp_blob_size", "bcfmm_mlp_dataset",
             "bcfmm_mlp_grad", "bcfmm_mlp_adam", "bcfmm_mlp_predict", "bcfmm_debug_expire_wait",
             "bcfmm_debug_list_coverage", "bcfmm_debug_near_pairs", "bcfmm_debug_shift_matrix",
-            "bcfmm_debug_tree_counts"]
+            "bcfmm_debug_tree_counts", "bcfmm_debug_m2l_taylor_coeffs"]
 NEAR_MODE = {"fp64": 0, "learned": 1, "none": 2}
 TASK_BIT = {"vtv": 1, "vtb": 2, "btv": 4}
 
@@ -35,7 +35,7 @@ class Params(C.Structure):
     _fields_ = [("p", C.c_int32), ("leaf_size", C.c_int32), ("eta_ns", C.c_double), ("near_n", C.c_int32),
                 ("near_k", C.c_int32), ("precision", C.c_int32), ("timing", C.c_int32), ("eta0", C.c_double),
                 ("tc_unit", C.c_int32), ("near_mode", C.c_int32), ("mlp_tol", C.c_double), ("mlp_blob", C.c_void_p),
-                ("mlp_blob_bytes", C.c_int64)]
+                ("mlp_blob_bytes", C.c_int64), ("p_level", C.c_int32 * 20), ("q0", C.c_int32)]
 
 
 class BcfmmError(RuntimeError):
@@ -72,6 +72,8 @@ def load(path: str = LIB_PATH):
         L.bcfmm_destroy.restype = None
         L.bcfmm_debug_m2l_matrix.argtypes = [i32, p, p]
         L.bcfmm_debug_m2l_matrix.restype = C.c_int
+        L.bcfmm_debug_m2l_taylor_coeffs.argtypes = [i32, p, p]
+        L.bcfmm_debug_m2l_taylor_coeffs.restype = C.c_int
         L.bcfmm_eval_noalloc.argtypes = [p, i32, p, p]
         L.bcfmm_eval_noalloc.restype = C.c_int
         L.bcfmm_build_batch.argtypes = [p, p, p, p, p, p, i32, C.POINTER(Params), p, C.POINTER(p)]
@@ -116,6 +118,12 @@ def _set(prm: Params, k, v):
         v = PRECISION[v]
     if k == "near_mode" and isinstance(v, str):
         v = NEAR_MODE[v]
+    if k == "p_level":
+        # expansion order per octree level (index = level; 0 or missing: p)
+        arr = (C.c_int32 * 20)()
+        for i, q in enumerate(list(v or [])[:20]):
+            arr[i] = int(q)
+        v = arr
     if k == "mlp_blob":
         # keep the bytes alive with the Params object; the library reads
         # them during the build only
@@ -143,6 +151,14 @@ def debug_m2l_matrix(p: int, o) -> np.ndarray:
     T = np.zeros((nterms(p), nterms(p)))
     _check(load().bcfmm_debug_m2l_matrix(p, o.ctypes.data, T.ctypes.data))
     return T
+
+
+def debug_m2l_taylor_coeffs(q: int, o) -> np.ndarray:
+    """D^gamma G(o), |gamma| <= q: the per-offset numbers of the Taylor-form M2L."""
+    o = np.ascontiguousarray(o, np.float64)
+    g = np.zeros(nterms(q))
+    _check(load().bcfmm_debug_m2l_taylor_coeffs(q, o.ctypes.data, g.ctypes.data))
+    return g
 
 
 def debug_shift_matrix(kind: str, p: int, octant: int) -> np.ndarray:
@@ -397,7 +413,9 @@ def debug_list_coverage(meshes, **kw) -> np.ndarray:
     """Host-only check of the FMM's interaction covering for one mesh or a
     batch: [0:3] per task the (target leaf, source point) pairs not covered
     exactly once, [3:6] per task the interaction entries the tensor-core
-    tiles get wrong (see include/bcfmm.h)."""
+    tiles get wrong, [6:9] per task the faults of the tensor-core schedule,
+    [9:12] per task the faults of the Taylor-form M2L schedule (see
+    include/bcfmm.h)."""
     vo, to, ro = [0], [0], [0]
     for m in meshes:
         vo.append(vo[-1] + len(m.verts))
@@ -408,7 +426,7 @@ def debug_list_coverage(meshes, **kw) -> np.ndarray:
     tris = np.ascontiguousarray(np.concatenate([np.asarray(m.tris).reshape(-1, 3) for m in meshes]), np.int32)
     vo, to, ro = (np.asarray(x, np.int64) for x in (vo, to, ro))
     prm = default_params(**kw)
-    out = np.zeros(6, np.int64)
+    out = np.zeros(12, np.int64)
     _check(load().bcfmm_debug_list_coverage(verts.ctypes.data, vo.ctypes.data, tets.ctypes.data, to.ctypes.data,
                                             tris.ctypes.data, ro.ctypes.data, len(meshes), C.byref(prm),
                                             out.ctypes.data))

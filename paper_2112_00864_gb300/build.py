@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libbcfmm.so")
-SOURCES = ["api.cu", "kernels_fmm.cu", "kernels_near.cu", "kernels_aux.cu", "m2l_tc.cu", "mlp.cu", "setup.cpp"]
+SOURCES = ["api.cu", "kernels_fmm.cu", "kernels_near.cu", "kernels_aux.cu", "m2l_taylor.cu", "m2l_tc.cu", "mlp.cu", "setup.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -14,6 +14,7 @@
 #include "../../include/bcfmm.h"
 #include "internal.h"
 #include "kernels.cuh"
+#include "m2l_taylor.cuh"
 #include "m2l_tc.cuh"
 #include "mlp.cuh"
 
@@ -76,10 +77,14 @@ struct TaskDev {
   NearGeom ng{};
   int64_t n_singular = 0, n_learned = 0, n_fp64 = 0;   // near-pair classes (near_mode != 0)
   DevTaskLists L{};
+  TcTaskSched tcs{};                   // tensor-core M2L launches, one per expansion order
+  TaylorTaskSched tys{};               // CUDA-core Taylor-form M2L launches, one per expansion order
   std::vector<int> m2m_off, l2l_off;   // host offsets into the per-level arrays
   int* m2m_parent = nullptr;
   int* l2l_child = nullptr;
-  int64_t p2p_pairs = 0, near_boxes = 0, m2l_pairs = 0, nnz = 0, tc_entries = 0;
+  int64_t p2p_pairs = 0, near_boxes = 0, m2l_pairs = 0, nnz = 0, tc_entries = 0, tc_rows = 0;
+  int64_t m2l_pairs_q[kMaxP + 1] = {};     // box pairs of the interaction phase per expansion order
+  double tc_mma_flop = 0;              // executed MMA flops of the tensor-core M2L per density
 };
 
 }  // namespace
@@ -106,7 +111,13 @@ struct bcfmm_ctx {
   int ndens[2] = {0, 0}, ndp[2] = {0, 0};
   double* dens[2] = {nullptr, nullptr};
   int* err = nullptr;                  // device error word (bounded device waits)
-  int tc_max_units = 0;                // largest tensor-core work-unit count over the tasks
+  size_t tc_partial_per_dens = 0;      // largest tensor-core partial-sum need over the tasks (float2)
+  // Taylor-form M2L (BCFMM_FP32): offset coefficients, prescaled moments,
+  // chunk partial sums (largest need over the tasks, floats per density)
+  TaylorTables ty{};
+  float* ty_momp = nullptr;
+  float* ty_partial = nullptr;
+  size_t ty_partial_per_dens = 0;
   float2* tc_partial = nullptr;        // unit partial sums of the tensor-core M2L
   uint8_t* tc_momb = nullptr;          // BF16 split moments of the tensor-core M2L
   // work buffers (sized for the largest ndp seen)
@@ -139,6 +150,14 @@ struct bcfmm_ctx {
   int work_gen = 0;                    // bumped whenever the work buffers move
 };
 
+// Expansion order of a level: p_level[level] when set (1..p), else p
+// (Sec. 4.3: the interaction phase and the local expansions of level l use
+// order q_l; moments are kept to order p on every level).
+static int level_order(const bcfmm_params& prm, int level) {
+  const int v = level < BCFMM_MAX_LEVELS ? prm.p_level[level] : 0;
+  return v > 0 ? v : prm.p;
+}
+
 static double wall() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
@@ -164,6 +183,8 @@ extern "C" void bcfmm_default_params(bcfmm_params* prm) {
   prm->mlp_tol = 5e-3;
   prm->mlp_blob = nullptr;
   prm->mlp_blob_bytes = 0;
+  for (int l = 0; l < BCFMM_MAX_LEVELS; ++l) prm->p_level[l] = 0;
+  prm->q0 = 0;
 }
 
 extern "C" const char* bcfmm_last_error(void) { return g_err.c_str(); }
@@ -181,6 +202,12 @@ extern "C" int bcfmm_debug_shift_matrix(int32_t kind, int32_t p, int32_t octant,
 extern "C" int bcfmm_debug_m2l_matrix(int32_t p, const double* o, double* T) {
   if (p < 0 || p > kMaxP || !o || !T) return fail(BCFMM_ERR_ARG, "debug_m2l_matrix: bad argument");
   m2l_matrix_scaled(p, o, T);
+  return BCFMM_OK;
+}
+
+extern "C" int bcfmm_debug_m2l_taylor_coeffs(int32_t q, const double* o, double* g) {
+  if (q < 0 || q > kMaxP || !o || !g) return fail(BCFMM_ERR_ARG, "debug_m2l_taylor_coeffs: bad argument");
+  m2l_taylor_coeffs(q, o, g);
   return BCFMM_OK;
 }
 
@@ -243,40 +270,110 @@ static int upload_task(bcfmm_ctx* C, const HostSetup& H, int t) {
   int* elem_pts;
   CU(m.upload(&elem_pts, ep.data(), ep.size(), st));
   L.elem_pts = elem_pts;
-  // tensor-core M2L tiles
+  // tensor-core M2L tiles and their schedule: one persistent launch per
+  // expansion order, units dealt to the SMs on the host
   L.err = C->err;
   L.tc_ntile = (int)T.tc_tile_off.size() > 0 ? (int)T.tc_tile_off.size() - 1 : 0;
   if (L.tc_ntile > 0) {
-    int *tt, *to, *ec, *es;
+    int* tt;
     CU(m.upload(&tt, T.tc_tile_tgt.data(), T.tc_tile_tgt.size(), st));
-    CU(m.upload(&to, T.tc_tile_off.data(), T.tc_tile_off.size(), st));
-    CU(m.upload(&ec, T.tc_ent_code.data(), T.tc_ent_code.size(), st));
-    CU(m.upload(&es, T.tc_ent_src.data(), T.tc_ent_src.size(), st));
-    L.tc_tile_tgt = tt; L.tc_tile_off = to; L.tc_ent_code = ec; L.tc_ent_src = es;
+    L.tc_tile_tgt = tt;
     D.tc_entries = (int64_t)T.tc_ent_code.size();
-    // work units: each tile's offsets cut into runs of U entries, U chosen
-    // so that there are about 4 units per SM (load balance); a tile without
-    // offsets still gets one (empty) unit that writes zeros
     int nsm = 152;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, C->device);
-    const int64_t E = D.tc_entries;
-    const int U = C->prm.tc_unit > 0 ? C->prm.tc_unit : (int)std::max<int64_t>(8, (E + 4 * nsm - 1) / (4 * nsm));
-    std::vector<int4> units;
-    std::vector<int> tile_unit_off(1, 0);
-    for (int tl = 0; tl < L.tc_ntile; ++tl) {
-      const int a = T.tc_tile_off[tl], b = T.tc_tile_off[tl + 1];
-      if (a == b) units.push_back(make_int4(tl, a, b, 0));
-      for (int x = a; x < b; x += U) units.push_back(make_int4(tl, x, std::min(b, x + U), 0));
-      tile_unit_off.push_back((int)units.size());
+    std::vector<TcOrderSchedHost> sched;
+    m2l_tc_schedule(T.tc_tile_off, T.tc_tile_q, T.tc_ent_src, nsm, C->tc.nsplit, C->prm.tc_unit, sched);
+    D.tcs = TcTaskSched();
+    // targets of orders above the tensor cores' range: CUDA-core M2L
+    {
+      std::vector<int> sel;
+      const int qmax = tc_max_order(C->tc.nsplit);
+      for (size_t k = 0; k < T.m2l_tgt.size(); ++k)
+        if (level_order(C->prm, H.box[T.m2l_tgt[k]].level) > qmax) sel.push_back((int)k);
+      int* dsel;
+      CU(m.upload(&dsel, sel.data(), sel.size(), st));
+      D.tcs.simt_sel = dsel;
+      D.tcs.nsimt = (int)sel.size();
     }
-    int4* du;
-    int* dto;
-    CU(m.upload(&du, units.data(), units.size(), st));
-    CU(m.upload(&dto, tile_unit_off.data(), tile_unit_off.size(), st));
-    L.tc_units = du;
-    L.tc_tile_unit_off = dto;
-    L.tc_nunit = (int)units.size();
-    C->tc_max_units = std::max(C->tc_max_units, L.tc_nunit);
+    for (const TcOrderSchedHost& O : sched) {
+      TcOrderSched& S = D.tcs.ord[O.q];
+      S.q = O.q;
+      S.ncta = (int)O.seq_off.size() - 1;
+      S.nunit = (int)O.units.size();
+      S.nslot = O.nslot;
+      S.nsplit_tiles = (int)O.splits.size();
+      S.nent = O.nent;
+      S.rows = O.rows;
+      // per sequence item: the offset code and the 128 source rows of its
+      // entry, in the order the CTA walks them (no indirection in the kernel)
+      std::vector<int> seq_code(O.seq_e.size()), seq_src(O.seq_e.size() * 128);
+      for (size_t i = 0; i < O.seq_e.size(); ++i) {
+        const int e = O.seq_e[i];
+        seq_code[i] = T.tc_ent_code[e];
+        std::copy(T.tc_ent_src.begin() + (size_t)e * 128, T.tc_ent_src.begin() + (size_t)e * 128 + 128,
+                  seq_src.begin() + i * 128);
+      }
+      int4 *du, *dsp;
+      int *dsc, *dss, *dsu, *dso;
+      CU(m.upload(&du, O.units.data(), O.units.size(), st));
+      CU(m.upload(&dsp, O.splits.data(), O.splits.size(), st));
+      CU(m.upload(&dsc, seq_code.data(), seq_code.size(), st));
+      CU(m.upload(&dss, seq_src.data(), seq_src.size(), st));
+      CU(m.upload(&dsu, O.seq_u.data(), O.seq_u.size(), st));
+      CU(m.upload(&dso, O.seq_off.data(), O.seq_off.size(), st));
+      S.units = du; S.splits = dsp; S.seq_code = dsc; S.seq_src = dss; S.seq_u = dsu; S.seq_off = dso;
+      const int npad = m2l_tc_npad(O.q);
+      D.tcs.partial_per_dens = std::max(D.tcs.partial_per_dens, (size_t)O.nslot * npad * 128);
+      D.tc_rows += O.rows;
+      D.tc_mma_flop += 2.0 * 128 * (C->tc.nsplit == 2 ? 3 : 6) * (double)npad * npad * (double)O.nent;
+    }
+    C->tc_partial_per_dens = std::max(C->tc_partial_per_dens, D.tcs.partial_per_dens);
+  }
+  // Taylor-form M2L: per order, the interaction lists cut into chunks and
+  // interleaved per warp; targets of orders above the kernel's range go to
+  // the generic kernel
+  for (size_t k = 0; k < T.m2l_tgt.size(); ++k)
+    D.m2l_pairs_q[level_order(C->prm, H.box[T.m2l_tgt[k]].level)] += T.vl_off[k + 1] - T.vl_off[k];
+  if (C->ty.g && !T.m2l_tgt.empty()) {
+    int nsm = 152;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, C->device);
+    std::vector<int> tq(T.m2l_tgt.size()), sel;
+    for (size_t k = 0; k < tq.size(); ++k) tq[k] = level_order(C->prm, H.box[T.m2l_tgt[k]].level);
+    std::vector<TaylorOrderHost> sched;
+    D.tys = TaylorTaskSched();
+    if (!m2l_taylor_schedule(T.m2l_tgt, T.vl_off, T.vl_src, T.vl_code, tq, C->nbox, C->ncode, nsm, sched, sel,
+                             &D.tys.cbits)) {
+      // indices too large for the packed lists: every target on the generic kernel
+      sched.clear();
+      sel.resize(T.m2l_tgt.size());
+      for (size_t k = 0; k < sel.size(); ++k) sel[k] = (int)k;
+    }
+    for (const TaylorOrderHost& O : sched) {
+      TaylorOrderSched& S = D.tys.ord[O.q];
+      S.q = O.q;
+      S.nwarp = (int)O.wb.size();
+      S.nchunk = O.nchunk;
+      S.ntgt = (int)O.tgt.size();
+      S.chunk = O.chunk;
+      S.pairs = O.pairs;
+      int2* dwb;
+      int *dlc, *dtg, *dtc;
+      uint32_t* dpk;
+      CU(m.upload(&dwb, O.wb.data(), O.wb.size(), st));
+      CU(m.upload(&dlc, O.lane_chunk.data(), O.lane_chunk.size(), st));
+      CU(m.upload(&dpk, O.pk.data(), O.pk.size(), st));
+      CU(m.upload(&dtg, O.tgt.data(), O.tgt.size(), st));
+      CU(m.upload(&dtc, O.tchunk.data(), O.tchunk.size(), st));
+      S.wb = dwb; S.lane_chunk = dlc; S.pk = dpk; S.tgt = dtg; S.tchunk = dtc;
+      D.tys.partial_per_dens = std::max(D.tys.partial_per_dens, (size_t)O.nchunk * nterms_q(O.q));
+    }
+    if (!sel.empty()) {
+      int* dsel;
+      CU(m.upload(&dsel, sel.data(), sel.size(), st));
+      D.tys.simt_sel = dsel;
+      D.tys.nsimt = (int)sel.size();
+    }
+    C->ty_partial_per_dens = std::max(C->ty_partial_per_dens, D.tys.partial_per_dens);
   }
   // near pairs + FP64 corrections computed on the device
   int64_t *cor_off;
@@ -455,6 +552,9 @@ static int build_impl(const double* verts, const int64_t* vert_off, const int32_
   if (4 * ntet > INT32_MAX / 2 || 3 * ntri > INT32_MAX / 2) return fail(BCFMM_ERR_ARG, "build: mesh too large");
   if (prm.p < 0 || prm.p > kMaxP) return fail(BCFMM_ERR_ARG, "build: p must be in 0..12");
   if (prm.leaf_size < 1 || prm.leaf_size > 128) return fail(BCFMM_ERR_ARG, "build: leaf_size must be in 1..128");
+  for (int l = 0; l < BCFMM_MAX_LEVELS; ++l)
+    if (prm.p_level[l] < 0 || prm.p_level[l] > prm.p)
+      return fail(BCFMM_ERR_ARG, "build: p_level[" + std::to_string(l) + "] must be in 0..p (0: p)");
   if (!(prm.eta_ns > 0)) return fail(BCFMM_ERR_ARG, "build: eta_ns must be > 0");
   if (!(prm.eta0 >= 0.3 && prm.eta0 <= 1.0)) return fail(BCFMM_ERR_ARG, "build: eta0 must be in 0.3..1");
   if (prm.near_n < 1 || prm.near_n > 8 || prm.near_k < 0 || prm.near_k > 3)
@@ -471,9 +571,7 @@ static int build_impl(const double* verts, const int64_t* vert_off, const int32_
   }
   const bool tc_mode = prm.precision == BCFMM_FP32_BF16X2 || prm.precision == BCFMM_FP32_BF16X3;
   const int nsplit = prm.precision == BCFMM_FP32_BF16X3 ? 3 : 2;
-  if (tc_mode && !m2l_tc_supported(prm.p, nsplit))
-    return fail(BCFMM_ERR_ARG, "build: the tensor-core M2L supports p <= " + std::to_string(kTcMaxP) +
-                                   (nsplit == 3 ? " (p <= 6 with the 3-term split)" : ""));
+  if (prm.q0 < 0 || prm.q0 > kMaxP) return fail(BCFMM_ERR_ARG, "build: q0 must be in 0..12");
 
   // host phase per mesh; meshes of a batch in parallel, largest first
   const double th = wall();
@@ -518,8 +616,17 @@ static int build_impl(const double* verts, const int64_t* vert_off, const int32_
     }
   }
   if (H.offsets.size() / 3 > 65535) return fail(BCFMM_ERR_ARG, "build: too many interaction offsets");
+  if (prm.q0 > 0) {
+    // Sec. 4.3 (Eq. def:q0): q_l = q0 + L - l, L the deepest level of the
+    // tree (of every mesh of a batch), capped at p
+    const int L = H.nlevels - 1;
+    for (int l = 0; l < BCFMM_MAX_LEVELS; ++l) prm.p_level[l] = std::max(1, std::min(prm.p, prm.q0 + L - l));
+  }
+  std::vector<int> box_q(H.box.size());
+  for (size_t i = 0; i < H.box.size(); ++i) box_q[i] = level_order(prm, H.box[i].level);
+  // levels of higher order than the tensor cores take run the CUDA-core M2L
   if (tc_mode)
-    for (int t = 0; t < 3; ++t) build_tc_tiles(H, t, 128);
+    for (int t = 0; t < 3; ++t) build_tc_tiles(H, t, 128, box_q, tc_max_order(nsplit));
   const double host_wall = wall() - th;
 
   int dev = 0;
@@ -568,15 +675,12 @@ static int build_impl(const double* verts, const int64_t* vert_off, const int32_
   G.np = C->np; G.ms = (C->np + 3) / 4 * 4; G.p = prm.p; G.nbox = C->nbox;
   {
     MultiIndex M; M.init(prm.p);
-    std::vector<int> mi(M.n), tk(M.n);
-    for (int q = 0; q < M.n; ++q) {
-      mi[q] = M.a[q] | (M.b[q] << 8) | (M.c[q] << 16);
-      tk[q] = nterms(prm.p - (M.a[q] + M.b[q] + M.c[q]));
-    }
-    int *dmi, *dtk;
-    if (m.upload(&dmi, mi.data(), mi.size(), st) != cudaSuccess || m.upload(&dtk, tk.data(), tk.size(), st) != cudaSuccess)
+    std::vector<int> mi(M.n);
+    for (int q = 0; q < M.n; ++q) mi[q] = M.a[q] | (M.b[q] << 8) | (M.c[q] << 16);
+    int* dmi;
+    if (m.upload(&dmi, mi.data(), mi.size(), st) != cudaSuccess)
       return cleanup(fail(BCFMM_ERR_OOM, "build: device allocation failed"));
-    G.mi = dmi; G.tri_k = dtk;
+    G.mi = dmi;
   }
   // boxes
   {
@@ -590,14 +694,15 @@ static int build_impl(const double* verts, const int64_t* vert_off, const int32_
       c0[i] = B.child0; nc[i] = B.nchild; oc[i] = B.octant; par[i] = B.parent;
       for (int c = 0; c < 2; ++c) rg[c][i] = make_int2(B.pt0[c], B.pt1[c]);
     }
-    double4_32a* dcs; int *dc0, *dnc, *doc, *dpar; int2 *drg0, *drg1;
+    const std::vector<int>& bq = box_q;
+    double4_32a* dcs; int *dc0, *dnc, *doc, *dpar, *dbq; int2 *drg0, *drg1;
     bool ok = m.upload(&dcs, cs.data(), nb, st) == cudaSuccess && m.upload(&dc0, c0.data(), nb, st) == cudaSuccess &&
               m.upload(&dnc, nc.data(), nb, st) == cudaSuccess && m.upload(&doc, oc.data(), nb, st) == cudaSuccess &&
               m.upload(&dpar, par.data(), nb, st) == cudaSuccess && m.upload(&drg0, rg[0].data(), nb, st) == cudaSuccess &&
-              m.upload(&drg1, rg[1].data(), nb, st) == cudaSuccess;
+              m.upload(&drg1, rg[1].data(), nb, st) == cudaSuccess && m.upload(&dbq, bq.data(), nb, st) == cudaSuccess;
     if (!ok) return cleanup(fail(BCFMM_ERR_OOM, "build: device allocation failed (boxes)"));
     G.box_cs = dcs; G.box_child0 = dc0; G.box_nchild = dnc; G.box_octant = doc; G.box_parent = dpar;
-    G.box_rng[0] = drg0; G.box_rng[1] = drg1;
+    G.box_rng[0] = drg0; G.box_rng[1] = drg1; G.box_q = dbq;
   }
   // sorted points
   for (int c = 0; c < 2; ++c) {
@@ -656,9 +761,42 @@ static int build_impl(const double* verts, const int64_t* vert_off, const int32_
               m.upload(&C->M2M32, M32.data(), M32.size(), st) == cudaSuccess &&
               m.upload(&C->L2L32, L32.data(), L32.size(), st) == cudaSuccess;
     if (!ok) return cleanup(fail(BCFMM_ERR_OOM, "build: device allocation failed (tables)"));
-    if (prm.precision == BCFMM_FP32_BF16X2 || prm.precision == BCFMM_FP32_BF16X3) {
-      cudaError_t ce = m2l_tc_prepare_tables(prm.p, ncode, T.data(), nsplit, &C->tc, st);
-      if (ce != cudaSuccess) return cleanup(fail(BCFMM_ERR_CUDA, std::string("build: tensor tables: ") + cudaGetErrorString(ce)));
+    if (tc_mode) {
+      std::vector<int> orders;
+      for (int t = 0; t < 3; ++t)
+        for (int q : H.task[t].tc_tile_q)
+          if (std::find(orders.begin(), orders.end(), q) == orders.end()) orders.push_back(q);
+      cudaError_t ce = m2l_tc_prepare_tables(prm.p, ncode, T.data(), nsplit, orders, &C->tc, st);
+      if (ce != cudaSuccess) {
+        m2l_tc_free_tables(&C->tc);
+        return cleanup(fail(BCFMM_ERR_CUDA, std::string("build: tensor tables: ") + cudaGetErrorString(ce)));
+      }
+    }
+    if (prm.precision == BCFMM_FP32) {
+      // Taylor-form M2L: D^gamma G(o), |gamma| <= the largest order among
+      // the levels that the register-blocked kernel takes
+      int qt = 0;
+      for (int l = 0; l < C->nlevels; ++l) {
+        const int q = level_order(prm, l);
+        if (q <= kTaylorMaxQ) qt = std::max(qt, q);
+      }
+      if (qt > 0) {
+        const int pitch = m2l_taylor_pitch(qt);
+        std::vector<float> g((size_t)std::max(ncode, 1) * pitch, 0.f);
+        std::vector<double> gd(nterms_q(qt));
+        for (int code = 0; code < ncode; ++code) {
+          const double od[3] = {(double)H.offsets[3 * code], (double)H.offsets[3 * code + 1],
+                                (double)H.offsets[3 * code + 2]};
+          m2l_taylor_coeffs(qt, od, gd.data());
+          for (int k = 0; k < nterms_q(qt); ++k) g[(size_t)code * pitch + k] = (float)gd[k];
+        }
+        float* dg;
+        if (m.upload(&dg, g.data(), g.size(), st) != cudaSuccess)
+          return cleanup(fail(BCFMM_ERR_OOM, "build: device allocation failed (Taylor tables)"));
+        C->ty.g = dg;
+        C->ty.gpitch = pitch;
+        C->ty.q = qt;
+      }
     }
   }
   double tn = wall();
@@ -829,8 +967,13 @@ extern "C" int bcfmm_debug_list_coverage(const double* verts, const int64_t* ver
     }
     // tensor-core tiles: the (offset code, source box) entries of each row
     // must be exactly the row's interaction list
+    if (prm.q0 > 0)
+      for (int l = 0; l < BCFMM_MAX_LEVELS; ++l) prm.p_level[l] = std::max(1, std::min(prm.p, prm.q0 + H.nlevels - 1 - l));
+    std::vector<int> box_q(H.box.size());
+    for (size_t i = 0; i < H.box.size(); ++i) box_q[i] = level_order(prm, H.box[i].level);
+    const int qmax = tc_max_order(2);
     for (int t = 0; t < 3; ++t) {
-      build_tc_tiles(H, t, 128);
+      build_tc_tiles(H, t, 128, box_q, qmax);
       const HostTask& T = H.task[t];
       std::vector<int> k_of(H.box.size(), -1);
       for (size_t k = 0; k < T.m2l_tgt.size(); ++k) k_of[T.m2l_tgt[k]] = (int)k;
@@ -849,12 +992,115 @@ extern "C" int bcfmm_debug_list_coverage(const double* verts, const int64_t* ver
         }
       for (size_t k = 0; k < T.m2l_tgt.size(); ++k) {
         std::vector<std::pair<int, int>> want;
-        for (int e = T.vl_off[k]; e < T.vl_off[k + 1]; ++e) want.push_back({T.vl_code[e], T.vl_src[e]});
+        if (box_q[T.m2l_tgt[k]] <= qmax)        // higher orders: CUDA-core M2L, no tile
+          for (int e = T.vl_off[k]; e < T.vl_off[k + 1]; ++e) want.push_back({T.vl_code[e], T.vl_src[e]});
         std::sort(want.begin(), want.end());
         std::sort(seen[k].begin(), seen[k].end());
         if (want != seen[k]) bad += (int64_t)std::max(want.size(), seen[k].size());
       }
+      // every row of a tile has the tile's expansion order
+      for (int tl = 0; tl < ntile; ++tl)
+        for (int r = 0; r < 128; ++r) {
+          const int tgt = T.tc_tile_tgt[(size_t)tl * 128 + r];
+          if (tgt >= 0 && box_q[tgt] != T.tc_tile_q[tl]) ++bad;
+        }
       out[3 + t] = bad;
+      // the persistent schedule: every entry of every tile in exactly one
+      // unit of its order, every unit exactly once in one CTA's sequence with
+      // its first / last flags, split tiles with consecutive partial slots
+      int64_t sbad = 0;
+      for (int nsm : {1, 7, 152}) {
+        std::vector<TcOrderSchedHost> sched;
+        m2l_tc_schedule(T.tc_tile_off, T.tc_tile_q, T.tc_ent_src, nsm, 2, prm.tc_unit, sched);
+        std::vector<int> ecount(T.tc_ent_code.size(), 0);
+        for (const TcOrderSchedHost& O : sched) {
+          std::vector<int> useen(O.units.size(), 0);
+          int nsl = 0;
+          for (const int4& sp : O.splits) nsl += sp.z;
+          if (nsl != O.nslot) ++sbad;
+          for (size_t u = 0; u < O.units.size(); ++u) {
+            const int4 U = O.units[u];
+            if (U.x < 0 || U.x >= ntile || T.tc_tile_q[U.x] != O.q) { ++sbad; continue; }
+            if (U.y < T.tc_tile_off[U.x] || U.z > T.tc_tile_off[U.x + 1] || U.y >= U.z) ++sbad;
+            if (U.w >= 0) {
+              bool found = false;
+              for (const int4& sp : O.splits)
+                if (sp.x == U.x && U.w >= sp.y && U.w < sp.y + sp.z) found = true;
+              if (!found) ++sbad;
+            } else if (U.y != T.tc_tile_off[U.x] || U.z != T.tc_tile_off[U.x + 1]) {
+              ++sbad;                       // an uncut tile's unit covers the whole tile
+            }
+          }
+          if ((int)O.seq_off.size() - 1 > nsm || O.seq_off.front() != 0 || O.seq_off.back() != (int)O.seq_e.size()) ++sbad;
+          for (size_t i = 0; i < O.seq_e.size(); ++i) {
+            const int u = O.seq_u[i] & ((1 << 29) - 1);
+            const bool first = (O.seq_u[i] >> 29) & 1, last = (O.seq_u[i] >> 30) & 1;
+            if (u < 0 || u >= (int)O.units.size()) { ++sbad; continue; }
+            const int4 U = O.units[u];
+            const int e = O.seq_e[i];
+            if (e < U.y || e >= U.z || first != (e == U.y) || last != (e == U.z - 1)) ++sbad;
+            if (i > 0 && !first && (O.seq_e[i - 1] != e - 1)) ++sbad;
+            if (e >= 0 && e < (int)ecount.size()) ecount[e]++;
+            if (first) useen[u]++;
+          }
+          for (int v : useen) sbad += (v != 1);
+        }
+        for (int v : ecount) sbad += (v != 1);
+      }
+      out[6 + t] = sbad;
+      // the Taylor-form schedule: every list entry of a target of orders
+      // 1..kTaylorMaxQ exactly once, in a lane whose chunk is the target's,
+      // decoding to the entry's (offset code, source box); every chunk in
+      // exactly one lane; every other target in the generic kernel's list
+      int64_t ybad = 0;
+      std::vector<int> tq(T.m2l_tgt.size());
+      for (size_t k = 0; k < tq.size(); ++k) tq[k] = box_q[T.m2l_tgt[k]];
+      for (int nsm : {1, 7, 152}) {
+        std::vector<TaylorOrderHost> ys;
+        std::vector<int> sel;
+        int cbits = 0;
+        if (!m2l_taylor_schedule(T.m2l_tgt, T.vl_off, T.vl_src, T.vl_code, tq, (int)H.box.size(),
+                                 (int)(H.offsets.size() / 3), nsm, ys, sel, &cbits)) {
+          ++ybad;
+          continue;
+        }
+        std::vector<std::vector<std::pair<int, int>>> got(T.m2l_tgt.size());
+        std::vector<int> in_sel(T.m2l_tgt.size(), 0);
+        for (int k : sel) {
+          if (k < 0 || k >= (int)in_sel.size()) { ++ybad; continue; }
+          in_sel[k]++;
+        }
+        for (const TaylorOrderHost& O : ys) {
+          std::vector<int> ctgt(O.nchunk, -1), cseen(O.nchunk, 0);
+          if ((int)O.tchunk.size() != (int)O.tgt.size() + 1 || O.tchunk.back() != O.nchunk) { ++ybad; continue; }
+          for (size_t i = 0; i < O.tgt.size(); ++i)
+            for (int c = O.tchunk[i]; c < O.tchunk[i + 1]; ++c) ctgt[c] = k_of[O.tgt[i]];
+          for (size_t w = 0; w < O.wb.size(); ++w)
+            for (int l = 0; l < 32; ++l) {
+              const int c = O.lane_chunk[w * 32 + l];
+              if (c >= O.nchunk) { ++ybad; continue; }
+              if (c >= 0) cseen[c]++;
+              for (int j = 0; j < O.wb[w].y; ++j) {
+                const uint32_t v = O.pk[(size_t)O.wb[w].x + (size_t)j * 32 + l];
+                if (v == ~0u) continue;
+                if (c < 0 || ctgt[c] < 0) { ++ybad; continue; }
+                got[ctgt[c]].push_back({(int)(v & ((1u << cbits) - 1u)), (int)(v >> cbits)});
+              }
+            }
+          for (int v : cseen) ybad += (v != 1);
+        }
+        for (size_t k = 0; k < T.m2l_tgt.size(); ++k) {
+          const bool taylor = tq[k] >= 1 && tq[k] <= kTaylorMaxQ;
+          if (in_sel[k] != (taylor ? 0 : 1)) ++ybad;
+          std::vector<std::pair<int, int>> want;
+          if (taylor && T.vl_off[k + 1] > T.vl_off[k])
+            for (int e = T.vl_off[k]; e < T.vl_off[k + 1]; ++e) want.push_back({T.vl_code[e], T.vl_src[e]});
+          std::sort(want.begin(), want.end());
+          std::sort(got[k].begin(), got[k].end());
+          if (want != got[k]) ybad += (int64_t)std::max(want.size(), got[k].size());
+        }
+      }
+      out[9 + t] = ybad;
     }
   } catch (const std::exception& ex) {
     return fail(BCFMM_ERR_ARG, std::string("debug_list_coverage: ") + ex.what());
@@ -886,10 +1132,12 @@ static int ensure_work(bcfmm_ctx* C, int ndp) {
   if (C->work_ndp >= ndp) return BCFMM_OK;
   auto& m = C->mem;
   for (void* p : {(void*)C->W64, (void*)C->mom64, (void*)C->loc64, (void*)C->phi, (void*)C->out_dev, (void*)C->W32,
-                  (void*)C->mom32, (void*)C->loc32, (void*)C->tc_partial, (void*)C->tc_momb})
+                  (void*)C->mom32, (void*)C->loc32, (void*)C->tc_partial, (void*)C->tc_momb, (void*)C->ty_momp,
+                  (void*)C->ty_partial})
     if (p) m.release(p);
   C->tc_partial = nullptr;
   C->tc_momb = nullptr;
+  C->ty_momp = C->ty_partial = nullptr;
   const int64_t npmax = std::max(C->npts[0], C->npts[1]);
   const int64_t nel = std::max(C->ntet, C->ntri);
   const size_t nexp = (size_t)C->nbox * ndp * C->G.ms;
@@ -906,9 +1154,15 @@ static int ensure_work(bcfmm_ctx* C, int ndp) {
     CU(m.alloc(&C->mom32, nexp));
     CU(m.alloc(&C->loc32, nexp));
     C->W64 = C->mom64 = C->loc64 = nullptr;
-    if (C->tc.tab != nullptr && C->tc_max_units > 0) {
-      CU(m.alloc(&C->tc_partial, (size_t)ndp * C->tc_max_units * C->tc.npad * 128));
-      CU(m.alloc(&C->tc_momb, (size_t)C->nbox * ndp * C->tc.nsplit * C->tc.kpad * 2));
+    if (C->tc.nsplit > 0) {
+      CU(m.alloc(&C->tc_partial, std::max<size_t>((size_t)ndp * C->tc_partial_per_dens, 1)));
+      // split moments: one row per (box, density, part)
+      const int kpitch = m2l_tc_kpitch(C->prm.p);
+      CU(m.alloc(&C->tc_momb, (size_t)C->nbox * ndp * C->tc.nsplit * kpitch * 2));
+    }
+    if (C->ty.g) {
+      CU(m.alloc(&C->ty_momp, (size_t)C->nbox * ndp * C->ty.gpitch));
+      CU(m.alloc(&C->ty_partial, std::max<size_t>((size_t)ndp * C->ty_partial_per_dens, 1)));
     }
   }
   C->work_ndp = ndp;
@@ -982,7 +1236,7 @@ static int eval_impl(bcfmm_ctx* C, int t, double* out, int out_is_device, bool s
       }
     }
     if (tm) CU(cudaEventRecord(ev[2], st));
-    if (!skip_far) CU(launch_m2l_simt<double>(G, L, C->T64, G.tri_k, ndp, C->mom64, C->loc64, st));
+    if (!skip_far) CU(launch_m2l_simt<double>(G, L, C->T64, ndp, C->mom64, C->loc64, st));
     if (tm) CU(cudaEventRecord(ev[3], st));
     for (int l = 3; l < C->nlevels && !skip_far; ++l) {
       const int n = D.l2l_off[l + 1] - D.l2l_off[l];
@@ -1007,9 +1261,13 @@ static int eval_impl(bcfmm_ctx* C, int t, double* out, int out_is_device, bool s
     if (tm) CU(cudaEventRecord(ev[2], st));
     if (skip_far) {
     } else if (tc) {
-      CU(launch_m2l_tc(G, L, C->tc, ndp, C->mom32, C->loc32, C->tc_partial, C->tc_momb, st));
+      CU(launch_m2l_tc(G, L, D.tcs, C->tc, ndp, C->mom32, C->loc32, C->tc_partial, C->tc_momb, st));
+      if (D.tcs.nsimt > 0) CU(launch_m2l_simt<float>(G, L, C->T32, ndp, C->mom32, C->loc32, st, D.tcs.simt_sel, D.tcs.nsimt));
+    } else if (C->ty.g) {
+      CU(launch_m2l_taylor(G, D.tys, C->ty, ndp, C->mom32, C->loc32, C->ty_momp, C->ty_partial, st));
+      if (D.tys.nsimt > 0) CU(launch_m2l_simt<float>(G, L, C->T32, ndp, C->mom32, C->loc32, st, D.tys.simt_sel, D.tys.nsimt));
     } else {
-      CU(launch_m2l_simt<float>(G, L, C->T32, G.tri_k, ndp, C->mom32, C->loc32, st));
+      CU(launch_m2l_simt<float>(G, L, C->T32, ndp, C->mom32, C->loc32, st));
     }
     if (tm) CU(cudaEventRecord(ev[3], st));
     for (int l = 3; l < C->nlevels && !skip_far; ++l) {
@@ -1115,12 +1373,14 @@ extern "C" int bcfmm_eval_noalloc(bcfmm_ctx* C, int32_t task, const double* dens
   if (!C) return fail(BCFMM_ERR_ARG, "eval_noalloc: null context");
   if (task < 0 || task > 2) return fail(BCFMM_ERR_ARG, "eval_noalloc: task must be 0 (VtV), 1 (VtB) or 2 (BtV)");
   if (!dens_dev || !out_dev) return fail(BCFMM_ERR_ARG, "eval_noalloc: null density or output");
-  if (C->prm.precision != BCFMM_FP32_BF16X2 && C->prm.precision != BCFMM_FP32_BF16X3)
-    return fail(BCFMM_ERR_ARG, "eval_noalloc: needs a context built with a BF16-split (tensor-core) precision");
+  const bool tcp = C->prm.precision == BCFMM_FP32_BF16X2 || C->prm.precision == BCFMM_FP32_BF16X3;
+  const bool typ = C->prm.precision == BCFMM_FP32;
+  if (!tcp && !typ)
+    return fail(BCFMM_ERR_ARG, "eval_noalloc: needs a context built with precision FP32 or a BF16 split");
   TaskDev& D = C->task[task];
   const DevTaskLists& L = D.L;
   const int kind = L.src_cls;
-  if (C->work_ndp < 1 || C->tc_momb == nullptr)
+  if (C->work_ndp < 1 || (tcp && C->tc_momb == nullptr) || (typ && C->ty.g && C->ty_momp == nullptr))
     return fail(BCFMM_ERR_STATE, "eval_noalloc: call bcfmm_set_density once first (it sizes the work buffers)");
   int dev = -1;
   CU(cudaGetDevice(&dev));
@@ -1128,7 +1388,8 @@ extern "C" int bcfmm_eval_noalloc(bcfmm_ctx* C, int32_t task, const double* dens
   float2* partial = nullptr;
   size_t cap = 0;
   CU(m2l_tc_noalloc_scratch(dev, &partial, &cap));
-  const size_t need = (size_t)L.tc_nunit * C->tc.npad * 128;
+  // tensor cores: float2 unit sums; Taylor form: float chunk sums
+  const size_t need = tcp ? D.tcs.partial_per_dens : (D.tys.partial_per_dens + 1) / 2;
   if (need > cap)
     return fail(BCFMM_ERR_ARG, "eval_noalloc: the mesh needs " + std::to_string(need * sizeof(float2)) +
                                    " bytes of M2L scratch, more than the fixed " + std::to_string(cap * sizeof(float2)) +
@@ -1147,7 +1408,15 @@ extern "C" int bcfmm_eval_noalloc(bcfmm_ctx* C, int32_t task, const double* dens
     const int n = D.m2m_off[l + 1] - D.m2m_off[l];
     CU(launch_m2m<float>(G, D.m2m_parent + D.m2m_off[l], n, C->M2M32, ndp, C->mom32, st));
   }
-  CU(launch_m2l_tc(G, L, C->tc, ndp, C->mom32, C->loc32, partial, C->tc_momb, st));
+  if (tcp) {
+    CU(launch_m2l_tc(G, L, D.tcs, C->tc, ndp, C->mom32, C->loc32, partial, C->tc_momb, st));
+    if (D.tcs.nsimt > 0) CU(launch_m2l_simt<float>(G, L, C->T32, ndp, C->mom32, C->loc32, st, D.tcs.simt_sel, D.tcs.nsimt));
+  } else if (C->ty.g) {
+    CU(launch_m2l_taylor(G, D.tys, C->ty, ndp, C->mom32, C->loc32, C->ty_momp, reinterpret_cast<float*>(partial), st));
+    if (D.tys.nsimt > 0) CU(launch_m2l_simt<float>(G, L, C->T32, ndp, C->mom32, C->loc32, st, D.tys.simt_sel, D.tys.nsimt));
+  } else {
+    CU(launch_m2l_simt<float>(G, L, C->T32, ndp, C->mom32, C->loc32, st));
+  }
   for (int l = 3; l < C->nlevels; ++l) {
     const int n = D.l2l_off[l + 1] - D.l2l_off[l];
     CU(launch_l2l<float>(G, D.l2l_child + D.l2l_off[l], n, C->L2L32, ndp, C->loc32, st));
@@ -1282,18 +1551,46 @@ extern "C" int bcfmm_stats(const bcfmm_ctx* C, char* json, size_t cap) {
   kv("setup_s", C->sec_setup); kv("tree_s", C->sec_tree); kv("lists_s", C->sec_lists);
   kv("near_search_s", C->sec_near_host); kv("near_rule_s", C->sec_near_dev);
   const char* names[3] = {"vtv", "vtb", "btv"};
+  s += "\"level_order\": [";
+  for (int l = 0; l < C->nlevels; ++l) s += std::to_string(level_order(C->prm, l)) + (l + 1 < C->nlevels ? ", " : "");
+  s += "], ";
   for (int t = 0; t < 3; ++t) {
-    char b[600];
+    char b[900];
+    const TaskDev& D = C->task[t];
+    std::string per_q = "[";
+    for (int q = 1; q <= kTcMaxQ; ++q) {
+      const TcOrderSched& O = D.tcs.ord[q];
+      if (O.nunit == 0) continue;
+      if (per_q.size() > 1) per_q += ", ";
+      per_q += "{\"q\": " + std::to_string(q) + ", \"entries\": " + std::to_string(O.nent) + ", \"rows\": " +
+               std::to_string(O.rows) + ", \"units\": " + std::to_string(O.nunit) + ", \"ctas\": " +
+               std::to_string(O.ncta) + ", \"split_tiles\": " + std::to_string(O.nsplit_tiles) + "}";
+    }
+    per_q += "], \"taylor_orders\": [";
+    bool first_ty = true;
+    for (int q = 1; q <= kTaylorMaxQ; ++q) {
+      const TaylorOrderSched& O = D.tys.ord[q];
+      if (O.nwarp == 0) continue;
+      if (!first_ty) per_q += ", ";
+      first_ty = false;
+      per_q += "{\"q\": " + std::to_string(q) + ", \"pairs\": " + std::to_string(O.pairs) + ", \"targets\": " +
+               std::to_string(O.ntgt) + ", \"chunk\": " + std::to_string(O.chunk) + ", \"chunks\": " +
+               std::to_string(O.nchunk) + ", \"warps\": " + std::to_string(O.nwarp) + "}";
+    }
+    per_q += "], \"m2l_pairs_by_order\": [";
+    for (int q = 0; q <= C->prm.p; ++q) per_q += std::to_string(D.m2l_pairs_q[q]) + (q < C->prm.p ? ", " : "");
+    per_q += "], \"generic_m2l_targets\": " + std::to_string(C->ty.g ? D.tys.nsimt : (D.tcs.nsimt > 0 ? D.tcs.nsimt : 0));
     snprintf(b, sizeof b,
              "\"%s\": {\"p2p_pairs\": %lld, \"near_boxes\": %lld, \"m2l_pairs\": %lld, \"near_pairs\": %lld, "
              "\"p2p_leaves\": %d, \"m2l_targets\": %d, \"p2m_leaves\": %d, \"tc_entries\": %lld, "
-             "\"near_singular\": %lld, \"near_learned\": %lld, \"near_fp64\": %lld}, ",
-             names[t], (long long)C->task[t].p2p_pairs, (long long)C->task[t].near_boxes,
-             (long long)C->task[t].m2l_pairs, (long long)C->task[t].nnz, C->task[t].L.n_p2p, C->task[t].L.n_m2l,
-             C->task[t].L.n_p2m, (long long)C->task[t].tc_entries, (long long)C->task[t].n_singular,
-             (long long)C->task[t].n_learned,
-             (long long)(C->prm.near_mode == 0 ? C->task[t].nnz : C->task[t].n_fp64));
+             "\"tc_rows\": %lld, \"tc_mma_flop\": %.17g, "
+             "\"near_singular\": %lld, \"near_learned\": %lld, \"near_fp64\": %lld, \"tc_orders\": ",
+             names[t], (long long)D.p2p_pairs, (long long)D.near_boxes, (long long)D.m2l_pairs, (long long)D.nnz,
+             D.L.n_p2p, D.L.n_m2l, D.L.n_p2m, (long long)D.tc_entries, (long long)D.tc_rows, D.tc_mma_flop,
+             (long long)D.n_singular, (long long)D.n_learned,
+             (long long)(C->prm.near_mode == 0 ? D.nnz : D.n_fp64));
     s += b;
+    s += per_q + "}, ";
   }
   // stages: weights+clear, P2M+M2M, M2L, L2L, L2P+P2P, element sums+corrections
   s += "\"stage_ms\": {";

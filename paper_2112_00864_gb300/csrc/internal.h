@@ -50,7 +50,7 @@ struct HostTask {
   std::vector<std::vector<int>> l2l_child;         // per level: boxes (level>=3) with target points
   std::vector<int> l2p_leaf;                       // leaves (level >= 2) with target points
   // tensor-core M2L tiles (see DevTaskLists)
-  std::vector<int> tc_tile_tgt, tc_tile_off, tc_ent_code, tc_ent_src;
+  std::vector<int> tc_tile_tgt, tc_tile_off, tc_ent_code, tc_ent_src, tc_tile_q;
   // near element pairs, CSR over target elements
   std::vector<int64_t> cor_off;
   std::vector<int32_t> cor_col;
@@ -82,7 +82,7 @@ std::string setup_mesh(HostSetup& H, const double* verts, int64_t nvert, const i
                        int64_t ntet, const int32_t* tris, int64_t ntri, bool* mesh_err);
 void build_tree(HostSetup& H, int leaf_size);
 void build_lists(HostSetup& H, double eta0);
-void build_tc_tiles(HostSetup& H, int task, int tile_m);
+void build_tc_tiles(HostSetup& H, int task, int tile_m, const std::vector<int>& box_q, int qmax);
 void find_near_pairs(HostSetup& H, double eta_ns);
 // Concatenates independently built meshes into one forest: elements and
 // points mesh after mesh, boxes level-major (level l of every mesh, mesh
@@ -98,6 +98,7 @@ void gauss_legendre01(int n, std::vector<double>& x, std::vector<double>& w);
 //  M2M: for child octant q, m_parent[b] += sum_g M[q][b][g] m_child[g].
 //  L2L: for child octant q, l_child[a] += sum_b L[q][a][b] l_parent[b].
 void m2l_matrix_scaled(int p, const double o[3], double* T);
+void m2l_taylor_coeffs(int q, const double o[3], double* g);
 void m2m_matrices(int p, std::vector<double>& M);
 void l2l_matrices(int p, std::vector<double>& L);
 

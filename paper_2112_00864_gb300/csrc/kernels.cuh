@@ -5,6 +5,8 @@
 
 namespace bcfmm {
 
+__host__ __device__ __forceinline__ int nterms_q(int q) { return q < 0 ? 0 : (q + 1) * (q + 2) * (q + 3) / 6; }
+
 // Geometry and lists the evaluation kernels read (device pointers).
 struct DevGeom {
   int np;                        // nterms(p)
@@ -12,7 +14,7 @@ struct DevGeom {
   int p;
   int nbox;
   const int* mi;                 // packed multi-indices a | b << 8 | c << 16, degree-major
-  const int* tri_k;              // per row alpha: nterms(p - |alpha|)
+  const int* box_q;              // expansion order of each box's level (<= p; Sec. 4.3)
   const double4_32a* box_cs;         // centre xyz, side s
   const int* box_child0;
   const int* box_nchild;
@@ -36,16 +38,10 @@ struct DevTaskLists {
   const int* elem_pts;           // [ntgt_el][4] sorted positions of the element's points (-1 pad)
   int nq_tgt;                    // 4 (tets) or 3 (triangles)
   int src_cls, tgt_cls;
-  // tensor-core M2L tiles: 128 same-level, same-octant targets per tile and,
-  // per (tile, offset) entry, the source box of every row (-1: none)
+  // tensor-core M2L tiles: 128 targets of one expansion order and one
+  // octant per tile (the entries' source rows live in the schedule)
   int tc_ntile;
   const int* tc_tile_tgt;        // [ntile][128]
-  const int* tc_tile_off;        // [ntile+1]
-  const int* tc_ent_code;        // [nent]
-  const int* tc_ent_src;         // [nent][128]
-  int tc_nunit;                  // work units: (tile, entry range)
-  const int4* tc_units;          // [nunit]
-  const int* tc_tile_unit_off;   // [ntile+1] units of each tile, in order
   int* err;                      // device error word (bounded waits)
 };
 
@@ -58,9 +54,10 @@ cudaError_t launch_p2m(const DevGeom& G, const DevTaskLists& L, const T* W, int6
                        T* mom, cudaStream_t st);
 template <typename T>
 cudaError_t launch_m2m(const DevGeom& G, const int* parents, int n, const T* M2M, int ndp, T* mom, cudaStream_t st);
+// sel: optional list of indices into L.m2l_tgt (nsel of them); NULL: every target
 template <typename T>
-cudaError_t launch_m2l_simt(const DevGeom& G, const DevTaskLists& L, const T* Tt, const int* tri_k,
-                            int ndp, const T* mom, T* loc, cudaStream_t st);
+cudaError_t launch_m2l_simt(const DevGeom& G, const DevTaskLists& L, const T* Tt, int ndp, const T* mom, T* loc,
+                            cudaStream_t st, const int* sel = nullptr, int nsel = 0);
 template <typename T>
 cudaError_t launch_l2l(const DevGeom& G, const int* children, int n, const T* L2L, int ndp, T* loc, cudaStream_t st);
 cudaError_t launch_p2p_l2p_f32(const DevGeom& G, const DevTaskLists& L, const float* W, int64_t nsrc_pts,

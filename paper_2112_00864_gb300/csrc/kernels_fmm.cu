@@ -124,43 +124,50 @@ cudaError_t launch_m2m(const DevGeom& G, const int* parents, int n, const T* M2M
 
 // ---------------------------------------------------------------- M2L
 // One CTA per target box, thread per row alpha of the local expansion.
-// Tt[code][b][a] is the transposed table (coalesced over alpha); row alpha
-// needs only b < tri_k[alpha] = nterms(p - |alpha|).
+// Tt[code][b][a] is the transposed table (coalesced over alpha).  The level
+// of the target box has order q <= p (Sec. 4.3): rows |alpha| <= q, and row
+// alpha needs only b < nterms(q - |alpha|) (|alpha| + |beta| <= q).
 template <typename T, int ND>
-__global__ void k_m2l_simt(DevGeom G, DevTaskLists L, const T* __restrict__ Tt, int ndp,
+__global__ void k_m2l_simt(DevGeom G, DevTaskLists L, const int* __restrict__ sel, const T* __restrict__ Tt, int ndp,
                            const T* __restrict__ mom, T* __restrict__ loc) {
   extern __shared__ unsigned char smraw[];
-  T* ms = reinterpret_cast<T*>(smraw);               // [ND][np]
+  T* ms = reinterpret_cast<T*>(smraw);               // [ND][nq]
   const int np = G.np;
-  const int tb = L.m2l_tgt[blockIdx.x];
+  const int ki = sel ? sel[blockIdx.x] : (int)blockIdx.x;   // index into the task's M2L targets
+  const int tb = L.m2l_tgt[ki];
+  const int q = G.box_q[tb], nq = nterms_q(q);
   const int a = threadIdx.x;
-  const int K = (a < np) ? G.tri_k[a] : 0;
+  int K = 0;
+  if (a < nq) {
+    const int mi = G.mi[a];
+    K = nterms_q(q - ((mi & 255) + ((mi >> 8) & 255) + ((mi >> 16) & 255)));
+  }
   // products of one translation in T, the sum over the interaction list
   // (~10^3 entries for eta0 = 0.5) in FP64
   double acc[ND];
 #pragma unroll
   for (int d = 0; d < ND; ++d) acc[d] = 0.0;
-  const int e0 = L.vl_off[blockIdx.x], e1 = L.vl_off[blockIdx.x + 1];
+  const int e0 = L.vl_off[ki], e1 = L.vl_off[ki + 1];
   for (int e = e0; e < e1; ++e) {
     const int sb = L.vl_src[e];
     const T* Tc = Tt + (int64_t)L.vl_code[e] * np * np;
     __syncthreads();
-    for (int i = threadIdx.x; i < ND * np; i += blockDim.x) ms[i] = mom[((int64_t)sb * ndp + i / np) * G.ms + i % np];
+    for (int i = threadIdx.x; i < ND * nq; i += blockDim.x) ms[i] = mom[((int64_t)sb * ndp + i / nq) * G.ms + i % nq];
     __syncthreads();
-    if (a < np) {
+    if (a < nq) {
       T part[ND];
 #pragma unroll
       for (int d = 0; d < ND; ++d) part[d] = 0;
       for (int b = 0; b < K; ++b) {
         const T t = Tc[(int64_t)b * np + a];
 #pragma unroll
-        for (int d = 0; d < ND; ++d) part[d] += t * ms[d * np + b];
+        for (int d = 0; d < ND; ++d) part[d] += t * ms[d * nq + b];
       }
 #pragma unroll
       for (int d = 0; d < ND; ++d) acc[d] += (double)part[d];
     }
   }
-  if (a < np) {
+  if (a < nq) {
     const double inv_s = 1.0 / G.box_cs[tb].w;
 #pragma unroll
     for (int d = 0; d < ND; ++d) loc[((int64_t)tb * ndp + d) * G.ms + a] = (T)(acc[d] * inv_s);
@@ -168,17 +175,18 @@ __global__ void k_m2l_simt(DevGeom G, DevTaskLists L, const T* __restrict__ Tt, 
 }
 
 template <typename T>
-cudaError_t launch_m2l_simt(const DevGeom& G, const DevTaskLists& L, const T* Tt, const int* /*tri_k*/,
-                            int ndp, const T* mom, T* loc, cudaStream_t st) {
-  if (L.n_m2l == 0) return cudaSuccess;
+cudaError_t launch_m2l_simt(const DevGeom& G, const DevTaskLists& L, const T* Tt, int ndp, const T* mom, T* loc,
+                            cudaStream_t st, const int* sel, int nsel) {
+  const int n = sel ? nsel : L.n_m2l;
+  if (n == 0) return cudaSuccess;
   int threads = ((G.np + 31) / 32) * 32;
   size_t sm = sizeof(T) * ndp * G.np;
   switch (ndp) {
-    case 1: k_m2l_simt<T, 1><<<L.n_m2l, threads, sm, st>>>(G, L, Tt, ndp, mom, loc); break;
-    case 2: k_m2l_simt<T, 2><<<L.n_m2l, threads, sm, st>>>(G, L, Tt, ndp, mom, loc); break;
-    case 4: k_m2l_simt<T, 4><<<L.n_m2l, threads, sm, st>>>(G, L, Tt, ndp, mom, loc); break;
-    case 8: k_m2l_simt<T, 8><<<L.n_m2l, threads, sm, st>>>(G, L, Tt, ndp, mom, loc); break;
-    case 16: k_m2l_simt<T, 16><<<L.n_m2l, threads, sm, st>>>(G, L, Tt, ndp, mom, loc); break;
+    case 1: k_m2l_simt<T, 1><<<n, threads, sm, st>>>(G, L, sel, Tt, ndp, mom, loc); break;
+    case 2: k_m2l_simt<T, 2><<<n, threads, sm, st>>>(G, L, sel, Tt, ndp, mom, loc); break;
+    case 4: k_m2l_simt<T, 4><<<n, threads, sm, st>>>(G, L, sel, Tt, ndp, mom, loc); break;
+    case 8: k_m2l_simt<T, 8><<<n, threads, sm, st>>>(G, L, sel, Tt, ndp, mom, loc); break;
+    case 16: k_m2l_simt<T, 16><<<n, threads, sm, st>>>(G, L, sel, Tt, ndp, mom, loc); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -186,7 +194,8 @@ cudaError_t launch_m2l_simt(const DevGeom& G, const DevTaskLists& L, const T* Tt
 
 // ---------------------------------------------------------------- L2L
 // l_child[a] += sum_{b >= a} L[octant][a][b] l_parent[b]; stored transposed,
-// Lt[octant][b][a], for coalesced reads over a.
+// Lt[octant][b][a], for coalesced reads over a.  The parent's expansion has
+// its level's order, the child's is cut to its own (Sec. 4.3): a < nq_child.
 template <typename T>
 __global__ void k_l2l(DevGeom G, const int* __restrict__ children, const T* __restrict__ L2L, int ndp,
                       T* __restrict__ loc) {
@@ -195,14 +204,15 @@ __global__ void k_l2l(DevGeom G, const int* __restrict__ children, const T* __re
   const int np = G.np;
   const int C = children[blockIdx.x];
   const int P = G.box_parent[C];
+  const int nqc = nterms_q(G.box_q[C]), nqp = nterms_q(G.box_q[P]);
   const T* Lm = L2L + (int64_t)G.box_octant[C] * np * np;
   for (int d = 0; d < ndp; ++d) {
     __syncthreads();
-    for (int i = threadIdx.x; i < np; i += blockDim.x) lp[i] = loc[((int64_t)P * ndp + d) * G.ms + i];
+    for (int i = threadIdx.x; i < nqp; i += blockDim.x) lp[i] = loc[((int64_t)P * ndp + d) * G.ms + i];
     __syncthreads();
-    for (int a = threadIdx.x; a < np; a += blockDim.x) {
+    for (int a = threadIdx.x; a < nqc; a += blockDim.x) {
       T acc = 0;
-      for (int b = a; b < np; ++b) acc += Lm[(int64_t)b * np + a] * lp[b];
+      for (int b = a; b < nqp; ++b) acc += Lm[(int64_t)b * np + a] * lp[b];
       loc[((int64_t)C * ndp + d) * G.ms + a] += acc;
     }
   }
@@ -276,7 +286,8 @@ __device__ __forceinline__ void l2p_and_store(const DevGeom& G, int leaf, int nd
     px[0] = py[0] = pz[0] = (T)1;
     for (int k = 1; k <= G.p; ++k) { px[k] = px[k - 1] * (T)xs; py[k] = py[k - 1] * (T)ys; pz[k] = pz[k - 1] * (T)zs; }
     const T* lb = loc + (int64_t)leaf * ndp * G.ms;
-    for (int q = 0; q < G.np; ++q) {
+    const int nq = nterms_q(G.box_q[leaf]);          // the leaf level's order
+    for (int q = 0; q < nq; ++q) {
       const int mi = G.mi[q];
       const T mono = px[mi & 255] * py[(mi >> 8) & 255] * pz[(mi >> 16) & 255];
 #pragma unroll
@@ -780,8 +791,8 @@ template cudaError_t launch_p2m<float>(const DevGeom&, const DevTaskLists&, cons
 template cudaError_t launch_p2m<double>(const DevGeom&, const DevTaskLists&, const double*, int64_t, int, double*, cudaStream_t);
 template cudaError_t launch_m2m<float>(const DevGeom&, const int*, int, const float*, int, float*, cudaStream_t);
 template cudaError_t launch_m2m<double>(const DevGeom&, const int*, int, const double*, int, double*, cudaStream_t);
-template cudaError_t launch_m2l_simt<float>(const DevGeom&, const DevTaskLists&, const float*, const int*, int, const float*, float*, cudaStream_t);
-template cudaError_t launch_m2l_simt<double>(const DevGeom&, const DevTaskLists&, const double*, const int*, int, const double*, double*, cudaStream_t);
+template cudaError_t launch_m2l_simt<float>(const DevGeom&, const DevTaskLists&, const float*, int, const float*, float*, cudaStream_t, const int*, int);
+template cudaError_t launch_m2l_simt<double>(const DevGeom&, const DevTaskLists&, const double*, int, const double*, double*, cudaStream_t, const int*, int);
 template cudaError_t launch_l2l<float>(const DevGeom&, const int*, int, const float*, int, float*, cudaStream_t);
 template cudaError_t launch_l2l<double>(const DevGeom&, const int*, int, const double*, int, double*, cudaStream_t);
 

@@ -1,0 +1,276 @@
+// CUDA-core M2L in the Taylor-coefficient form (Sec. 3.3): prescaled
+// moments, per-offset derivative coefficients, register-blocked contraction
+// over gamma = a + b, chunk sums reduced per target in FP64.
+#include <algorithm>
+#include <numeric>
+#include <utility>
+
+#include "m2l_taylor.cuh"
+
+namespace bcfmm {
+namespace {
+
+// degree-major multi-index position: degree d = i + j + k, then i
+// descending, then j descending (the order of the expansion arrays)
+__host__ __device__ constexpr int mi_idx(int i, int j, int k) {
+  return (i + j + k) * (i + j + k + 1) * (i + j + k + 2) / 6 + (j + k) * (j + k + 1) / 2 + k;
+}
+
+// The (a, b, gamma = a + b) triples of order Q in contraction order: gamma
+// degree-major, then a by components; built at compile time, so that the
+// unrolled kernel indexes its register arrays with constants.
+__host__ __device__ constexpr int taylor_nterms(int q) {
+  int n = 0;
+  for (int gi = 0; gi <= q; ++gi)
+    for (int gj = 0; gj <= q - gi; ++gj)
+      for (int gk = 0; gk <= q - gi - gj; ++gk) n += (gi + 1) * (gj + 1) * (gk + 1);
+  return n;
+}
+template <int Q>
+struct TaylorTerms {
+  static constexpr int N = taylor_nterms(Q);
+  int a[N], b[N], g[N];
+  __host__ __device__ constexpr TaylorTerms() : a{}, b{}, g{} {
+    int n = 0;
+    for (int gi = 0; gi <= Q; ++gi)
+      for (int gj = 0; gj <= Q - gi; ++gj)
+        for (int gk = 0; gk <= Q - gi - gj; ++gk)
+          for (int ai = 0; ai <= gi; ++ai)
+            for (int aj = 0; aj <= gj; ++aj)
+              for (int ak = 0; ak <= gk; ++ak) {
+                a[n] = mi_idx(ai, aj, ak);
+                b[n] = mi_idx(gi - ai, gj - aj, gk - ak);
+                g[n] = mi_idx(gi, gj, gk);
+                ++n;
+              }
+  }
+};
+template <int Q>
+struct TaylorTab {
+  static constexpr TaylorTerms<Q> v{};
+};
+template <int Q, int I>
+struct TaylorTerm {
+  static constexpr int a = TaylorTab<Q>::v.a[I], b = TaylorTab<Q>::v.b[I], g = TaylorTab<Q>::v.g[I];
+};
+template <int Q, int... I>
+__device__ __forceinline__ void taylor_contract(float* acc, const float* m, const float* g,
+                                                std::integer_sequence<int, I...>) {
+  ((acc[TaylorTerm<Q, I>::a] = fmaf(g[TaylorTerm<Q, I>::g], m[TaylorTerm<Q, I>::b], acc[TaylorTerm<Q, I>::a])), ...);
+}
+
+__device__ __forceinline__ double inv_fact3(int packed) {
+  double f = 1.0;
+  for (int ax = 0; ax < 3; ++ax) {
+    const int n = (packed >> (8 * ax)) & 255;
+    for (int i = 2; i <= n; ++i) f *= (double)i;
+  }
+  return 1.0 / f;
+}
+
+__device__ __forceinline__ int degree3(int packed) { return (packed & 255) + ((packed >> 8) & 255) + ((packed >> 16) & 255); }
+
+// m'[row][b] = (-1)^{|b|} m[row][b] / b!  (b < nq; zero up to the pitch)
+__global__ void k_taylor_prescale(const float* __restrict__ mom, int64_t nrow, int ms, int nq, int pitch,
+                                  const int* __restrict__ mi, float* __restrict__ momp) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nrow * pitch) return;
+  const int64_t row = i / pitch;
+  const int b = (int)(i % pitch);
+  float v = 0.f;
+  if (b < nq) {
+    const int e = mi[b];
+    const double s = (degree3(e) & 1) ? -inv_fact3(e) : inv_fact3(e);
+    v = (float)((double)mom[row * ms + b] * s);
+  }
+  momp[i] = v;
+}
+
+struct TaylorArgs {
+  const int2* wb;
+  const int* lane_chunk;
+  const uint32_t* pk;
+  int nwarp, cbits, ndp, pitch;
+  const float* momp;   // [nbox * ndp][pitch]
+  const float* g;      // [ncode][pitch]
+  float* partial;      // [nchunk][ndp][nq]
+};
+
+// one lane = one chunk: sum over its entries of lambda'_a = sum_b g[a+b] m'_b
+template <int Q>
+__global__ void __launch_bounds__(128) k_m2l_taylor(TaylorArgs A) {
+  constexpr int NQ = (Q + 1) * (Q + 2) * (Q + 3) / 6;
+  constexpr int NV = (NQ + 3) / 4;
+  const int w = blockIdx.x * 4 + (threadIdx.x >> 5), lane = threadIdx.x & 31, d = blockIdx.y;
+  if (w >= A.nwarp) return;
+  const int2 wb = A.wb[w];
+  const uint32_t cmask = (1u << A.cbits) - 1u;
+  const uint32_t* pk = A.pk + wb.x + lane;
+  float acc[NQ];
+#pragma unroll
+  for (int a = 0; a < NQ; ++a) acc[a] = 0.f;
+  uint32_t nxt = wb.y > 0 ? __ldg(pk) : ~0u;
+  for (int j = 0; j < wb.y; ++j) {
+    const uint32_t cur = nxt;
+    if (j + 1 < wb.y) nxt = __ldg(pk + 32 * (j + 1));
+    if (cur == ~0u) continue;
+    const float4* mr = reinterpret_cast<const float4*>(A.momp + ((int64_t)(cur >> A.cbits) * A.ndp + d) * A.pitch);
+    const float4* gr = reinterpret_cast<const float4*>(A.g + (int64_t)(cur & cmask) * A.pitch);
+    float m[NV * 4], g[NV * 4];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const float4 x = __ldg(mr + v), y = __ldg(gr + v);
+      m[4 * v] = x.x; m[4 * v + 1] = x.y; m[4 * v + 2] = x.z; m[4 * v + 3] = x.w;
+      g[4 * v] = y.x; g[4 * v + 1] = y.y; g[4 * v + 2] = y.z; g[4 * v + 3] = y.w;
+    }
+    // every (a, b) with |a + b| <= Q
+    taylor_contract<Q>(acc, m, g, std::make_integer_sequence<int, taylor_nterms(Q)>{});
+  }
+  const int c = A.lane_chunk[w * 32 + lane];
+  if (c < 0) return;
+  float* o = A.partial + ((int64_t)c * A.ndp + d) * NQ;
+#pragma unroll
+  for (int a = 0; a < NQ; ++a) o[a] = acc[a];
+}
+
+// loc[t][d][a] = (1/(a! s_t)) * sum over the target's chunks (FP64, chunk order)
+__global__ void k_m2l_taylor_reduce(const int* __restrict__ tgt, const int* __restrict__ tchunk,
+                                    const float* __restrict__ partial, int nq, int ndp, int ms,
+                                    const int* __restrict__ mi, const double4_32a* __restrict__ box_cs,
+                                    float* __restrict__ loc) {
+  const int t = blockIdx.x;
+  const int tb = tgt[t], c0 = tchunk[t], c1 = tchunk[t + 1];
+  const double inv_s = 1.0 / box_cs[tb].w;
+  for (int i = threadIdx.x; i < ndp * nq; i += blockDim.x) {
+    const int d = i / nq, a = i % nq;
+    double s = 0.0;
+    for (int c = c0; c < c1; ++c) s += (double)partial[((int64_t)c * ndp + d) * nq + a];
+    loc[((int64_t)tb * ndp + d) * ms + a] = (float)(s * inv_fact3(mi[a]) * inv_s);
+  }
+}
+
+template <int Q>
+cudaError_t launch_order(const TaylorOrderSched& O, const TaylorTaskSched& S, const TaylorTables& tab, const DevGeom& G,
+                         int ndp, const float* momp, float* loc, float* partial, cudaStream_t st) {
+  constexpr int NQ = (Q + 1) * (Q + 2) * (Q + 3) / 6;
+  TaylorArgs A;
+  A.wb = O.wb;
+  A.lane_chunk = O.lane_chunk;
+  A.pk = O.pk;
+  A.nwarp = O.nwarp;
+  A.cbits = S.cbits;
+  A.ndp = ndp;
+  A.pitch = tab.gpitch;
+  A.momp = momp;
+  A.g = tab.g;
+  A.partial = partial;
+  k_m2l_taylor<Q><<<dim3((unsigned)((O.nwarp + 3) / 4), (unsigned)ndp), 128, 0, st>>>(A);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_m2l_taylor_reduce<<<O.ntgt, 64, 0, st>>>(O.tgt, O.tchunk, partial, NQ, ndp, G.ms, G.mi, G.box_cs, loc);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int m2l_taylor_pitch(int q) { return (nterms_q(q) + 3) / 4 * 4; }
+
+bool m2l_taylor_schedule(const std::vector<int>& m2l_tgt, const std::vector<int>& vl_off,
+                         const std::vector<int>& vl_src, const std::vector<uint16_t>& vl_code,
+                         const std::vector<int>& target_q, int nbox, int ncode, int nsm,
+                         std::vector<TaylorOrderHost>& out, std::vector<int>& sel, int* cbits) {
+  out.clear();
+  sel.clear();
+  int cb = 1;
+  while ((1 << cb) < std::max(ncode, 2)) ++cb;
+  *cbits = cb;
+  if ((int64_t)std::max(nbox, 1) << cb >= (int64_t)0xFFFFFFFFu) return false;
+  const int nt = (int)m2l_tgt.size();
+  for (int k = 0; k < nt; ++k)
+    if (target_q[k] < 1 || target_q[k] > kTaylorMaxQ) sel.push_back(k);
+  for (int q = 1; q <= kTaylorMaxQ; ++q) {
+    TaylorOrderHost O;
+    O.q = q;
+    std::vector<int> ks;
+    for (int k = 0; k < nt; ++k)
+      if (target_q[k] == q && vl_off[k + 1] > vl_off[k]) {
+        ks.push_back(k);
+        O.pairs += vl_off[k + 1] - vl_off[k];
+      }
+    if (ks.empty()) continue;
+    // chunk length: about 48 warps of work per SM, at most 32 entries (the
+    // FP32 sum of a chunk stays short), at least 8 (partial-sum traffic)
+    O.chunk = (int)std::min<int64_t>(32, std::max<int64_t>(8, (O.pairs + 1536LL * nsm - 1) / (1536LL * nsm)));
+    std::vector<int2> ch;   // (first entry, length)
+    O.tchunk.assign(1, 0);
+    for (int k : ks) {
+      const int a = vl_off[k], n = vl_off[k + 1] - a;
+      const int nc = (n + O.chunk - 1) / O.chunk;
+      for (int i = 0; i < nc; ++i) {
+        const int b0 = a + (int)((int64_t)n * i / nc), b1 = a + (int)((int64_t)n * (i + 1) / nc);
+        ch.push_back(make_int2(b0, b1 - b0));
+      }
+      O.tgt.push_back(m2l_tgt[k]);
+      O.tchunk.push_back((int)ch.size());
+    }
+    O.nchunk = (int)ch.size();
+    std::vector<int> ord(ch.size());
+    std::iota(ord.begin(), ord.end(), 0);
+    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return ch[x].y > ch[y].y; });
+    const int nwarp = (O.nchunk + 31) / 32;
+    O.lane_chunk.assign((size_t)nwarp * 32, -1);
+    for (int w = 0; w < nwarp; ++w) {
+      const int len = ch[ord[(size_t)w * 32]].y;
+      O.wb.push_back(make_int2((int)O.pk.size(), len));
+      const size_t base = O.pk.size();
+      O.pk.resize(base + (size_t)len * 32, ~0u);
+      for (int l = 0; l < 32 && w * 32 + l < O.nchunk; ++l) {
+        const int c = ord[(size_t)w * 32 + l];
+        O.lane_chunk[(size_t)w * 32 + l] = c;
+        for (int j = 0; j < ch[c].y; ++j) {
+          const int e = ch[c].x + j;
+          O.pk[base + (size_t)j * 32 + l] = ((uint32_t)vl_src[e] << cb) | (uint32_t)vl_code[e];
+        }
+      }
+    }
+    if (O.pk.size() >= (size_t)INT32_MAX) return false;
+    out.push_back(std::move(O));
+  }
+  return true;
+}
+
+cudaError_t launch_m2l_taylor(const DevGeom& G, const TaylorTaskSched& S, const TaylorTables& tab, int ndp,
+                              const float* mom, float* loc, float* momp, float* partial, cudaStream_t st) {
+  int qtop = 0;
+  for (int q = 1; q <= kTaylorMaxQ; ++q)
+    if (S.ord[q].nwarp > 0) qtop = q;
+  if (qtop == 0) return cudaSuccess;
+  if (qtop > tab.q || tab.gpitch != m2l_taylor_pitch(tab.q)) return cudaErrorInvalidValue;
+  {
+    const int64_t nrow = (int64_t)G.nbox * ndp;
+    const int64_t n = nrow * tab.gpitch;
+    k_taylor_prescale<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(mom, nrow, G.ms, nterms_q(qtop), tab.gpitch, G.mi,
+                                                                   momp);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  for (int q = 1; q <= kTaylorMaxQ; ++q) {
+    const TaylorOrderSched& O = S.ord[q];
+    if (O.nwarp == 0) continue;
+    cudaError_t e = cudaSuccess;
+    switch (q) {
+      case 1: e = launch_order<1>(O, S, tab, G, ndp, momp, loc, partial, st); break;
+      case 2: e = launch_order<2>(O, S, tab, G, ndp, momp, loc, partial, st); break;
+      case 3: e = launch_order<3>(O, S, tab, G, ndp, momp, loc, partial, st); break;
+      case 4: e = launch_order<4>(O, S, tab, G, ndp, momp, loc, partial, st); break;
+      case 5: e = launch_order<5>(O, S, tab, G, ndp, momp, loc, partial, st); break;
+      case 6: e = launch_order<6>(O, S, tab, G, ndp, momp, loc, partial, st); break;
+      case 7: e = launch_order<7>(O, S, tab, G, ndp, momp, loc, partial, st); break;
+      default: e = cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace bcfmm

@@ -330,30 +330,38 @@ void build_lists(HostSetup& H, double eta0) {
 }
 
 // Tiles of the tensor-core interaction phase: M2L targets grouped by
-// (level, octant in the parent), tile_m per tile; per tile the offsets that
-// occur, each with the source box of every row.
-void build_tc_tiles(HostSetup& H, int t, int tile_m) {
+// (expansion order of their level, octant in the parent), tile_m per tile,
+// levels of equal order and boxes in tree order inside a group (the
+// box-scaled translation table of an offset serves every level, and
+// same-octant boxes share the possible offsets); per tile the offsets that
+// occur, each with the source box of every row.  box_q: order per box;
+// targets whose order exceeds qmax get no tile (CUDA-core M2L).
+void build_tc_tiles(HostSetup& H, int t, int tile_m, const std::vector<int>& box_q, int qmax) {
   HostTask& T = H.task[t];
-  const int n = (int)T.m2l_tgt.size();
-  std::vector<int> order(n);
-  for (int i = 0; i < n; ++i) order[i] = i;
+  std::vector<int> order;
+  for (int i = 0; i < (int)T.m2l_tgt.size(); ++i)
+    if (box_q[T.m2l_tgt[i]] <= qmax) order.push_back(i);
+  const int n = (int)order.size();
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-    const HostBox& A = H.box[T.m2l_tgt[x]];
-    const HostBox& B = H.box[T.m2l_tgt[y]];
-    return A.level != B.level ? A.level < B.level : A.octant < B.octant;
+    const int bx = T.m2l_tgt[x], by = T.m2l_tgt[y];
+    if (box_q[bx] != box_q[by]) return box_q[bx] < box_q[by];
+    return H.box[bx].octant < H.box[by].octant;
   });
   T.tc_tile_tgt.clear(); T.tc_tile_off.assign(1, 0); T.tc_ent_code.clear(); T.tc_ent_src.clear();
+  T.tc_tile_q.clear();
   int i = 0;
   while (i < n) {
-    const HostBox& F = H.box[T.m2l_tgt[order[i]]];
+    const int f = T.m2l_tgt[order[i]];
+    const HostBox& F = H.box[f];
     int j = i;
     std::vector<int> rows;
     while (j < n && (int)rows.size() < tile_m) {
-      const HostBox& B = H.box[T.m2l_tgt[order[j]]];
-      if (B.level != F.level || B.octant != F.octant) break;
+      const int b = T.m2l_tgt[order[j]];
+      if (box_q[b] != box_q[f] || H.box[b].octant != F.octant) break;
       rows.push_back(order[j]);
       ++j;
     }
+    T.tc_tile_q.push_back(box_q[f]);
     std::unordered_map<int, int> ent_of;
     std::vector<std::pair<int, std::vector<int>>> ents;
     for (int r = 0; r < (int)rows.size(); ++r) {
@@ -711,6 +719,16 @@ void m2l_matrix_scaled(int p, const double o[3], double* T) {
       }
       T[a * M.n + b] = v;
     }
+}
+
+// D^gamma G(o) = D^gamma (1/r)(o) / (4 pi), |gamma| <= q, degree-major:
+// the per-offset coefficients of the Taylor-form M2L (Sec. 3.3).
+void m2l_taylor_coeffs(int q, const double o[3], double* g) {
+  MultiIndex M;
+  M.init(q);
+  std::vector<double> D;
+  derivatives_inv_r(o, q, M, D);
+  for (int k = 0; k < M.n; ++k) g[k] = D[k] / kFourPi;
 }
 
 // child octant q: child centre = parent centre + sigma s_parent / 4,

@@ -88,7 +88,7 @@ def test_tensor_core_m2l_matches_oracle(bc, c1, prec, task):
     r2, rm = rel(u, ref, _sizes(m, task))
     assert r2 <= 1e-6, (r2, rm)
     r2, rm = rel(u, O.direct(task, m, dens), _sizes(m, task))
-    assert r2 <= 1.5e-6, (r2, rm)
+    assert r2 <= 1e-6, (r2, rm)
 
 
 @pytest.mark.parametrize("p,prec", [(2, "bf16x2"), (3, "bf16x2"), (4, "bf16x2"), (5, "bf16x2"), (7, "bf16x2"),
@@ -170,16 +170,21 @@ def test_degenerate_meshes(bc):
 
 def test_ball_full_size_sampled(bc):
     """Config-2 workload (unit ball, 5120 boundary triangles, ~1.9e5 tets)
-    in the benchmark's launch configuration (p = 6, eta0 = 0.5, leaf 128,
-    BF16x2 tensor-core M2L) against O1 on sampled target elements."""
+    in the benchmark's launch configuration (the chosen form: BF16x2
+    tensor-core M2L, the paper's order schedule q0 = 4 capped at p = 7,
+    eta0 = 0.5; VtV + VtB through one CUDA graph) against O1 on 512
+    sampled target elements per task: rel L2 <= 5e-7."""
+    import bench
     m = ball_bc_mesh(4, radial=0.35)
     f = np.ones((1, m.ntet))
-    ctx = bc.Context.from_mesh(m, p=6, eta0=0.5, leaf_size=128, precision="bf16x2")
-    ctx.set_density(bc.VOLUME, f)
+    ctx = bc.Context.from_mesh(m, **bench.CHOSEN)
+    ctx.set_density(bc.VOLUME, torch.tensor(f, device="cuda"))
+    outs = ctx.eval_graph(("vtv", "vtb"))
+    assert ctx.stats()["device_error"] == 0
     rng = np.random.default_rng(11)
     for task, nel, size in (("vtv", m.ntet, O.element_volumes(m)), ("vtb", m.ntri, O.element_areas(m))):
-        u = ctx.eval(task).cpu().numpy()[0]
-        idx = np.sort(rng.choice(nel, 96, replace=False))
+        u = outs[task].cpu().numpy()[0]
+        idx = np.sort(rng.choice(nel, 512, replace=False))
         ref = O.direct(task, m, f, targets=idx)[0]
         r2, rm = rel(u[idx], ref, size[idx])
-        assert r2 <= 1e-6, (task, r2, rm)
+        assert r2 <= 5e-7, (task, r2, rm)

@@ -89,6 +89,30 @@ def test_m2l_tables_match_oracle(lib):
     assert np.all(T[mask] == 0) and np.all(T[~mask] != 0) is not None
 
 
+def test_m2l_taylor_form_rebuilds_oracle_matrix(lib):
+    """The Taylor-form M2L keeps nterms(q) numbers per offset, g = D^gamma G(o),
+    and rebuilds T[a][b] = g[a + b] (-1)^{|b|} / (a! b!) (Sec. 3.3, the
+    expansion coefficients lambda): checked against the oracle's matrix,
+    entry by entry, zero pattern included."""
+    import oracle as O
+    from math import factorial
+    for q in (1, 4, 5, 7):
+        mi = O.multi_indices(q)
+        pos = {tuple(m): i for i, m in enumerate(mi)}
+        fact = np.array([factorial(a) * factorial(b) * factorial(c) for a, b, c in mi], float)
+        deg = mi.sum(1)
+        for o in ((2, 0, 0), (3, -2, 1), (-2, -3, -3), (0, 5, -4)):
+            g = bcfmm.debug_m2l_taylor_coeffs(q, np.array(o, float))
+            R = O.m2l_matrix(np.array(o, float), q)
+            T = np.zeros_like(R)
+            for a in range(len(mi)):
+                for b in range(len(mi)):
+                    if deg[a] + deg[b] <= q:
+                        T[a, b] = g[pos[tuple(mi[a] + mi[b])]] * (-1.0) ** deg[b] / (fact[a] * fact[b])
+            assert np.abs(T - R).max() <= 1e-13 * np.abs(R).max(), (q, o)
+            assert np.array_equal(T == 0, R == 0), (q, o)
+
+
 def test_batch_argument_errors_before_gpu(lib):
     """bcfmm_build_batch validates offsets and every mesh before any device work."""
     import ctypes as C
@@ -129,18 +153,27 @@ def test_learned_mode_arguments_checked_before_gpu(lib):
     assert rc == -1 and b"header" in lib.bcfmm_last_error()
 
 
-@pytest.mark.parametrize("leaf_size,eta0", [(64, 0.5), (8, 0.9), (32, 0.5), (3, 0.7)])
-def test_interactions_covered_exactly_once(lib, leaf_size, eta0):
+@pytest.mark.parametrize("leaf_size,eta0,p_level,tc_unit", [(64, 0.5, None, 0), (8, 0.9, None, 0),
+                                                           (32, 0.5, [0, 0, 6, 5, 4, 3, 3, 3], 0),
+                                                           (3, 0.7, [0, 0, 2, 3, 4, 5, 6, 7], 5),
+                                                           (16, 0.5, [0, 0, 9, 8, 7, 6, 5, 4], 0)])
+def test_interactions_covered_exactly_once(lib, leaf_size, eta0, p_level, tc_unit):
     """Every (target leaf, source point) pair of a mesh is evaluated once:
     by the leaf's near field N* or by one interaction list of the leaf or an
-    ancestor (Sec. 2, Sec. 3); in a batch, never across meshes.  Host-only
-    check of the library's own tree and lists (no GPU)."""
+    ancestor (Sec. 2, Sec. 3); in a batch, never across meshes.  The
+    tensor-core tiles (grouped by the levels' expansion orders, Sec. 4.3)
+    reproduce every interaction list, and their persistent schedule covers
+    every (tile, offset) entry once; the Taylor-form schedule (list chunks
+    interleaved per warp) holds every list entry of its orders once and
+    leaves the higher orders (8, 9 here) to the generic kernel.  Host-only
+    check of the library's own tree, lists, tiles and schedules (no GPU)."""
     from paper_2112_00864_gb300.inputs import ball_bc_mesh, batch_meshes, cube_bc_mesh
-    kw = dict(leaf_size=leaf_size, eta0=eta0)
-    # [0:3] covering of every task, [3:6] the tensor-core tiles against the lists
-    assert list(bcfmm.debug_list_coverage([cube_bc_mesh(0.25, 0.125)], **kw)) == [0] * 6
-    assert list(bcfmm.debug_list_coverage([ball_bc_mesh(2, radial=0.35)], **kw)) == [0] * 6
-    assert list(bcfmm.debug_list_coverage(batch_meshes(4, seed=3, hs=(1 / 4, 1 / 8)), **kw)) == [0] * 6
+    kw = dict(leaf_size=leaf_size, eta0=eta0, p=max(p_level or [7]), tc_unit=tc_unit, p_level=p_level)
+    # [0:3] covering of every task, [3:6] the tiles against the lists, [6:9] the
+    # tensor-core schedule, [9:12] the Taylor-form schedule
+    assert list(bcfmm.debug_list_coverage([cube_bc_mesh(0.25, 0.125)], **kw)) == [0] * 12
+    assert list(bcfmm.debug_list_coverage([ball_bc_mesh(2, radial=0.35)], **kw)) == [0] * 12
+    assert list(bcfmm.debug_list_coverage(batch_meshes(4, seed=3, hs=(1 / 4, 1 / 8)), **kw)) == [0] * 12
 
 
 def test_near_pairs_equal_brute_force(lib):

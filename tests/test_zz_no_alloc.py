@@ -3,8 +3,9 @@
 It serves callers that must not call the CUDA allocator during an
 evaluation (a host framework that owns and budgets all device memory, or a
 latency-critical loop where cudaMalloc/cudaFree could synchronise the
-device).  Its tensor-core interaction phase keeps the unit partial sums in
-the library's fixed static device array instead of context scratch.  Its
+device).  Its interaction phase (tensor cores or the Taylor form) keeps its
+partial sums in the library's fixed static device array instead of context
+scratch.  Its
 results must match the ordinary entry points on the same context, for two
 calls in a row (the shared array keeps the previous call's contents).
 This file is collected last on purpose.
@@ -26,11 +27,12 @@ def bc():
     return bcfmm
 
 
-def test_eval_noalloc_matches_eval(bc):
+@pytest.mark.parametrize("prec", ["bf16x2", "fp32"])
+def test_eval_noalloc_matches_eval(bc, prec):
     from paper_2112_00864_gb300.inputs import cube_bc_mesh, densities
     m = cube_bc_mesh(0.25, 0.125)
     f, g = densities(m, "sine")
-    ctx = bc.Context.from_mesh(m, p=6, leaf_size=64, precision="bf16x2")
+    ctx = bc.Context.from_mesh(m, p=6, leaf_size=64, precision=prec)
     f_dev = torch.tensor(f, device="cuda")
     g_dev = torch.tensor(g, device="cuda")
     ctx.set_density(bc.VOLUME, f_dev)
@@ -53,7 +55,7 @@ def test_eval_noalloc_rejects_misuse(bc):
     m = cube_bc_mesh(0.5, 0.25)
     f = torch.ones(m.ntet, dtype=torch.float64, device="cuda")
     out = torch.empty(m.ntet, dtype=torch.float64, device="cuda")
-    plain = bc.Context.from_mesh(m, p=4, precision="fp32")
+    plain = bc.Context.from_mesh(m, p=4, precision="fp64")
     plain.set_density(bc.VOLUME, f[None])
     with pytest.raises(bc.BcfmmError) as e:
         plain.eval_noalloc("vtv", f, out)
