@@ -274,6 +274,21 @@ static int upload_task(bcfmm_ctx* C, const HostSetup& H, int t) {
   // expansion order, units dealt to the SMs on the host
   L.err = C->err;
   L.tc_ntile = (int)T.tc_tile_off.size() > 0 ? (int)T.tc_tile_off.size() - 1 : 0;
+  D.tcs = TcTaskSched();
+  if (C->tc.nsplit > 0) {
+    // targets of orders above the tensor cores' range: CUDA-core M2L (also
+    // when no level's order is in range and there are no tiles at all)
+    std::vector<int> sel;
+    const int qmax = tc_max_order(C->tc.nsplit);
+    for (size_t k = 0; k < T.m2l_tgt.size(); ++k)
+      if (level_order(C->prm, H.box[T.m2l_tgt[k]].level) > qmax) sel.push_back((int)k);
+    if (!sel.empty()) {
+      int* dsel;
+      CU(m.upload(&dsel, sel.data(), sel.size(), st));
+      D.tcs.simt_sel = dsel;
+      D.tcs.nsimt = (int)sel.size();
+    }
+  }
   if (L.tc_ntile > 0) {
     int* tt;
     CU(m.upload(&tt, T.tc_tile_tgt.data(), T.tc_tile_tgt.size(), st));
@@ -283,18 +298,6 @@ static int upload_task(bcfmm_ctx* C, const HostSetup& H, int t) {
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, C->device);
     std::vector<TcOrderSchedHost> sched;
     m2l_tc_schedule(T.tc_tile_off, T.tc_tile_q, T.tc_ent_src, nsm, C->tc.nsplit, C->prm.tc_unit, sched);
-    D.tcs = TcTaskSched();
-    // targets of orders above the tensor cores' range: CUDA-core M2L
-    {
-      std::vector<int> sel;
-      const int qmax = tc_max_order(C->tc.nsplit);
-      for (size_t k = 0; k < T.m2l_tgt.size(); ++k)
-        if (level_order(C->prm, H.box[T.m2l_tgt[k]].level) > qmax) sel.push_back((int)k);
-      int* dsel;
-      CU(m.upload(&dsel, sel.data(), sel.size(), st));
-      D.tcs.simt_sel = dsel;
-      D.tcs.nsimt = (int)sel.size();
-    }
     for (const TcOrderSchedHost& O : sched) {
       TcOrderSched& S = D.tcs.ord[O.q];
       S.q = O.q;
@@ -790,10 +793,23 @@ static int build_impl(const double* verts, const int64_t* vert_off, const int32_
           m2l_taylor_coeffs(qt, od, gd.data());
           for (int k = 0; k < nterms_q(qt); ++k) g[(size_t)code * pitch + k] = (float)gd[k];
         }
-        float* dg;
-        if (m.upload(&dg, g.data(), g.size(), st) != cudaSuccess)
+        // (-1)^{|b|} / b! for the moments, 1 / a! for the locals
+        std::vector<float> fac(2 * (size_t)pitch, 0.f);
+        MultiIndex M;
+        M.init(qt);
+        for (int k = 0; k < M.n; ++k) {
+          double f = 1.0;
+          for (int n = 2; n <= M.a[k]; ++n) f *= n;
+          for (int n = 2; n <= M.b[k]; ++n) f *= n;
+          for (int n = 2; n <= M.c[k]; ++n) f *= n;
+          fac[k] = (float)(((M.a[k] + M.b[k] + M.c[k]) & 1 ? -1.0 : 1.0) / f);
+          fac[pitch + k] = (float)(1.0 / f);
+        }
+        float *dg, *df;
+        if (m.upload(&dg, g.data(), g.size(), st) != cudaSuccess || m.upload(&df, fac.data(), fac.size(), st) != cudaSuccess)
           return cleanup(fail(BCFMM_ERR_OOM, "build: device allocation failed (Taylor tables)"));
         C->ty.g = dg;
+        C->ty.fac = df;
         C->ty.gpitch = pitch;
         C->ty.q = qt;
       }

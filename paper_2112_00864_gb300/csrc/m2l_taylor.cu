@@ -1,6 +1,6 @@
 // CUDA-core M2L in the Taylor-coefficient form (Sec. 3.3): prescaled
 // moments, per-offset derivative coefficients, register-blocked contraction
-// over gamma = a + b, chunk sums reduced per target in FP64.
+// over gamma = a + b, chunk sums reduced per target (compensated FP32).
 #include <algorithm>
 #include <numeric>
 #include <utility>
@@ -59,31 +59,28 @@ __device__ __forceinline__ void taylor_contract(float* acc, const float* m, cons
   ((acc[TaylorTerm<Q, I>::a] = fmaf(g[TaylorTerm<Q, I>::g], m[TaylorTerm<Q, I>::b], acc[TaylorTerm<Q, I>::a])), ...);
 }
 
-__device__ __forceinline__ double inv_fact3(int packed) {
-  double f = 1.0;
-  for (int ax = 0; ax < 3; ++ax) {
-    const int n = (packed >> (8 * ax)) & 255;
-    for (int i = 2; i <= n; ++i) f *= (double)i;
-  }
-  return 1.0 / f;
+__device__ __forceinline__ void two_sum(float& hi, float& lo, float x) {
+  const float t = hi + x;
+  const float b = t - hi;
+  lo += (hi - (t - b)) + (x - b);
+  hi = t;
 }
 
-__device__ __forceinline__ int degree3(int packed) { return (packed & 255) + ((packed >> 8) & 255) + ((packed >> 16) & 255); }
-
-// m'[row][b] = (-1)^{|b|} m[row][b] / b!  (b < nq; zero up to the pitch)
+// m'[row][b] = m[row][b] * fac[b], fac[b] = (-1)^{|b|} / b!  (b < nq; zero up to the pitch)
 __global__ void k_taylor_prescale(const float* __restrict__ mom, int64_t nrow, int ms, int nq, int pitch,
-                                  const int* __restrict__ mi, float* __restrict__ momp) {
+                                  const float* __restrict__ fac, float* __restrict__ momp) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= nrow * pitch) return;
   const int64_t row = i / pitch;
   const int b = (int)(i % pitch);
-  float v = 0.f;
-  if (b < nq) {
-    const int e = mi[b];
-    const double s = (degree3(e) & 1) ? -inv_fact3(e) : inv_fact3(e);
-    v = (float)((double)mom[row * ms + b] * s);
-  }
-  momp[i] = v;
+  momp[i] = b < nq ? mom[row * ms + b] * fac[b] : 0.f;
+}
+
+// 32-byte read-only load (eight floats; the address is 32-byte aligned)
+__device__ __forceinline__ void ldg8(const float* p, float* v) {
+  asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+      : "l"(p));
 }
 
 struct TaylorArgs {
@@ -100,7 +97,9 @@ struct TaylorArgs {
 template <int Q>
 __global__ void __launch_bounds__(128) k_m2l_taylor(TaylorArgs A) {
   constexpr int NQ = (Q + 1) * (Q + 2) * (Q + 3) / 6;
-  constexpr int NV = (NQ + 3) / 4;
+  // 32-byte loads up to order 5; 16-byte loads above (fewer live registers)
+  constexpr int W = Q <= 5 ? 8 : 4;
+  constexpr int NV = (NQ + W - 1) / W;
   const int w = blockIdx.x * 4 + (threadIdx.x >> 5), lane = threadIdx.x & 31, d = blockIdx.y;
   if (w >= A.nwarp) return;
   const int2 wb = A.wb[w];
@@ -114,14 +113,20 @@ __global__ void __launch_bounds__(128) k_m2l_taylor(TaylorArgs A) {
     const uint32_t cur = nxt;
     if (j + 1 < wb.y) nxt = __ldg(pk + 32 * (j + 1));
     if (cur == ~0u) continue;
-    const float4* mr = reinterpret_cast<const float4*>(A.momp + ((int64_t)(cur >> A.cbits) * A.ndp + d) * A.pitch);
-    const float4* gr = reinterpret_cast<const float4*>(A.g + (int64_t)(cur & cmask) * A.pitch);
-    float m[NV * 4], g[NV * 4];
+    const float* mr = A.momp + ((int64_t)(cur >> A.cbits) * A.ndp + d) * A.pitch;
+    const float* gr = A.g + (int64_t)(cur & cmask) * A.pitch;
+    float m[NV * W], g[NV * W];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      const float4 x = __ldg(mr + v), y = __ldg(gr + v);
-      m[4 * v] = x.x; m[4 * v + 1] = x.y; m[4 * v + 2] = x.z; m[4 * v + 3] = x.w;
-      g[4 * v] = y.x; g[4 * v + 1] = y.y; g[4 * v + 2] = y.z; g[4 * v + 3] = y.w;
+      if constexpr (W == 8) {
+        ldg8(mr + 8 * v, m + 8 * v);
+        ldg8(gr + 8 * v, g + 8 * v);
+      } else {
+        const float4 x = __ldg(reinterpret_cast<const float4*>(mr) + v);
+        const float4 y = __ldg(reinterpret_cast<const float4*>(gr) + v);
+        m[4 * v] = x.x; m[4 * v + 1] = x.y; m[4 * v + 2] = x.z; m[4 * v + 3] = x.w;
+        g[4 * v] = y.x; g[4 * v + 1] = y.y; g[4 * v + 2] = y.z; g[4 * v + 3] = y.w;
+      }
     }
     // every (a, b) with |a + b| <= Q
     taylor_contract<Q>(acc, m, g, std::make_integer_sequence<int, taylor_nterms(Q)>{});
@@ -133,20 +138,24 @@ __global__ void __launch_bounds__(128) k_m2l_taylor(TaylorArgs A) {
   for (int a = 0; a < NQ; ++a) o[a] = acc[a];
 }
 
-// loc[t][d][a] = (1/(a! s_t)) * sum over the target's chunks (FP64, chunk order)
-__global__ void k_m2l_taylor_reduce(const int* __restrict__ tgt, const int* __restrict__ tchunk,
-                                    const float* __restrict__ partial, int nq, int ndp, int ms,
-                                    const int* __restrict__ mi, const double4_32a* __restrict__ box_cs,
-                                    float* __restrict__ loc) {
-  const int t = blockIdx.x;
+// loc[t][d][a] = post[a] / s_t * (sum over the target's chunks, in chunk
+// order, compensated), post[a] = 1 / a!; one thread per (target, d, a)
+__global__ void __launch_bounds__(128) k_m2l_taylor_reduce(int ntgt, const int* __restrict__ tgt,
+                                                          const int* __restrict__ tchunk,
+                                                          const float* __restrict__ partial, int nq, int ndp, int ms,
+                                                          const float* __restrict__ post,
+                                                          const double4_32a* __restrict__ box_cs,
+                                                          float* __restrict__ loc) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int per = ndp * nq;
+  if (i >= (int64_t)ntgt * per) return;
+  const int t = (int)(i / per), r = (int)(i % per), d = r / nq, a = r % nq;
   const int tb = tgt[t], c0 = tchunk[t], c1 = tchunk[t + 1];
-  const double inv_s = 1.0 / box_cs[tb].w;
-  for (int i = threadIdx.x; i < ndp * nq; i += blockDim.x) {
-    const int d = i / nq, a = i % nq;
-    double s = 0.0;
-    for (int c = c0; c < c1; ++c) s += (double)partial[((int64_t)c * ndp + d) * nq + a];
-    loc[((int64_t)tb * ndp + d) * ms + a] = (float)(s * inv_fact3(mi[a]) * inv_s);
-  }
+  float hi = 0.f, lo = 0.f;
+  const float* pp = partial + (int64_t)d * nq + a;
+#pragma unroll 4
+  for (int c = c0; c < c1; ++c) two_sum(hi, lo, __ldg(pp + (int64_t)c * per));
+  loc[((int64_t)tb * ndp + d) * ms + a] = (hi + lo) * post[a] / (float)box_cs[tb].w;
 }
 
 template <int Q>
@@ -167,13 +176,15 @@ cudaError_t launch_order(const TaylorOrderSched& O, const TaylorTaskSched& S, co
   k_m2l_taylor<Q><<<dim3((unsigned)((O.nwarp + 3) / 4), (unsigned)ndp), 128, 0, st>>>(A);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_m2l_taylor_reduce<<<O.ntgt, 64, 0, st>>>(O.tgt, O.tchunk, partial, NQ, ndp, G.ms, G.mi, G.box_cs, loc);
+  const int64_t n = (int64_t)O.ntgt * ndp * NQ;
+  k_m2l_taylor_reduce<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(O.ntgt, O.tgt, O.tchunk, partial, NQ, ndp, G.ms,
+                                                                   tab.fac + tab.gpitch, G.box_cs, loc);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-int m2l_taylor_pitch(int q) { return (nterms_q(q) + 3) / 4 * 4; }
+int m2l_taylor_pitch(int q) { return (nterms_q(q) + 7) / 8 * 8; }
 
 bool m2l_taylor_schedule(const std::vector<int>& m2l_tgt, const std::vector<int>& vl_off,
                          const std::vector<int>& vl_src, const std::vector<uint16_t>& vl_code,
@@ -249,7 +260,7 @@ cudaError_t launch_m2l_taylor(const DevGeom& G, const TaylorTaskSched& S, const 
   {
     const int64_t nrow = (int64_t)G.nbox * ndp;
     const int64_t n = nrow * tab.gpitch;
-    k_taylor_prescale<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(mom, nrow, G.ms, nterms_q(qtop), tab.gpitch, G.mi,
+    k_taylor_prescale<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(mom, nrow, G.ms, nterms_q(qtop), tab.gpitch, tab.fac,
                                                                    momp);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -1,5 +1,5 @@
 // CUDA-core M2L of the boundary-concentrated FMM in the Taylor-coefficient
-// form (FP32 products, FP64 sums over work chunks).
+// form (FP32 products, compensated sums over work chunks).
 #pragma once
 #include <cuda_runtime.h>
 
@@ -30,8 +30,8 @@ constexpr int kTaylorMaxQ = 7;
 // dealt 32 to a warp (one per lane), and the lane's entries are interleaved
 // with its warp's others (entry j of lane l at pk[first + 32 j + l]) so that
 // every index load is one coalesced line.  A chunk's FP32 sum goes to its
-// own partial slot; a second kernel adds a target's slots in FP64, in chunk
-// order (deterministic), and stores the local expansion.
+// own partial slot; a second kernel adds a target's slots in chunk order
+// (compensated FP32 sum, deterministic) and stores the local expansion.
 struct TaylorOrderSched {
   int q = 0, nwarp = 0, nchunk = 0, ntgt = 0, chunk = 0;
   int64_t pairs = 0;
@@ -65,12 +65,16 @@ bool m2l_taylor_schedule(const std::vector<int>& m2l_tgt, const std::vector<int>
                          const std::vector<int>& target_q, int nbox, int ncode, int nsm,
                          std::vector<TaylorOrderHost>& out, std::vector<int>& sel, int* cbits);
 
-// Offset coefficients g_o (FP32, [ncode][gpitch], |gamma| <= q).
+// Offset coefficients g_o (FP32, [ncode][gpitch], |gamma| <= q) and the
+// multi-index factors fac[0..gpitch) = (-1)^{|b|} / b! (moments),
+// fac[gpitch..2 gpitch) = 1 / a! (locals).
 struct TaylorTables {
   const float* g = nullptr;
+  const float* fac = nullptr;
   int gpitch = 0, q = 0;
 };
-// row pitch (floats) of the prescaled moments and of g for order q
+// row pitch (floats, a multiple of 8: rows are read as 32-byte pieces) of
+// the prescaled moments and of g for order q
 int m2l_taylor_pitch(int q);
 
 // Scratch (device memory owned by the caller):
