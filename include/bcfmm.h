@@ -384,6 +384,16 @@ int bcfmm_debug_shift_matrix(int32_t kind, int32_t p, int32_t octant, double* ou
 int bcfmm_debug_expire_wait(bcfmm_ctx* ctx, int32_t spins);
 
 /*
+ * Measured FP32 FMA throughput of CUDA device `device` (flop/s, an FMA
+ * counted as 2): a probe kernel of independent FMA chains on every SM,
+ * timed with CUDA events (best of three after a warm-up, ~ms).  The paper
+ * has no counterpart; it is the denominator check for the roofline of
+ * the CUDA-core passes.  flops: host double.  Synchronises the device.
+ * Errors: BCFMM_ERR_ARG, BCFMM_ERR_CUDA.
+ */
+int bcfmm_measure_ffma(int32_t device, double* flops);
+
+/*
  * Test hook, host only (no GPU, no context): boxes and leaves per level of
  * the octree the build makes for one mesh with the given leaf size (root =
  * bounding cube of the vertices; a box holding more than leaf_size points

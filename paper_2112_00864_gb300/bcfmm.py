@@ -26,7 +26,7 @@ EXPORTED = ["bcfmm_default_params", "bcfmm_build_bc_tree", "bcfmm_set_density", 
             "bcfmm_build_like", "bcfmm_direct_sample", "bcfmm_mlp_blob_size", "bcfmm_mlp_dataset",
             "bcfmm_mlp_grad", "bcfmm_mlp_adam", "bcfmm_mlp_predict", "bcfmm_debug_expire_wait",
             "bcfmm_debug_list_coverage", "bcfmm_debug_near_pairs", "bcfmm_debug_shift_matrix",
-            "bcfmm_debug_tree_counts", "bcfmm_debug_m2l_taylor_coeffs"]
+            "bcfmm_debug_tree_counts", "bcfmm_debug_m2l_taylor_coeffs", "bcfmm_measure_ffma"]
 NEAR_MODE = {"fp64": 0, "learned": 1, "none": 2}
 TASK_BIT = {"vtv": 1, "vtb": 2, "btv": 4}
 
@@ -74,6 +74,8 @@ def load(path: str = LIB_PATH):
         L.bcfmm_debug_m2l_matrix.restype = C.c_int
         L.bcfmm_debug_m2l_taylor_coeffs.argtypes = [i32, p, p]
         L.bcfmm_debug_m2l_taylor_coeffs.restype = C.c_int
+        L.bcfmm_measure_ffma.argtypes = [i32, p]
+        L.bcfmm_measure_ffma.restype = C.c_int
         L.bcfmm_eval_noalloc.argtypes = [p, i32, p, p]
         L.bcfmm_eval_noalloc.restype = C.c_int
         L.bcfmm_build_batch.argtypes = [p, p, p, p, p, p, i32, C.POINTER(Params), p, C.POINTER(p)]
@@ -151,6 +153,13 @@ def debug_m2l_matrix(p: int, o) -> np.ndarray:
     T = np.zeros((nterms(p), nterms(p)))
     _check(load().bcfmm_debug_m2l_matrix(p, o.ctypes.data, T.ctypes.data))
     return T
+
+
+def measure_ffma(device: int = 0) -> float:
+    """Measured FP32 FMA throughput of a CUDA device in flop/s (FMA = 2)."""
+    out = C.c_double(0.0)
+    _check(load().bcfmm_measure_ffma(device, C.byref(out)))
+    return out.value
 
 
 def debug_m2l_taylor_coeffs(q: int, o) -> np.ndarray:

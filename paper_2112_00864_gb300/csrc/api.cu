@@ -1538,6 +1538,17 @@ extern "C" int bcfmm_mlp_predict(const float* params, const float* feat, const f
   return BCFMM_OK;
 }
 
+extern "C" int bcfmm_measure_ffma(int32_t device, double* flops) {
+  if (!flops) return fail(BCFMM_ERR_ARG, "measure_ffma: null output");
+  int cur = -1;
+  CU(cudaGetDevice(&cur));
+  if (device != cur) CU(cudaSetDevice(device));
+  const cudaError_t e = measure_ffma_rate(device, flops);
+  if (device != cur) cudaSetDevice(cur);
+  if (e != cudaSuccess) return fail(BCFMM_ERR_CUDA, std::string("measure_ffma: ") + cudaGetErrorString(e));
+  return BCFMM_OK;
+}
+
 extern "C" int bcfmm_debug_expire_wait(bcfmm_ctx* C, int32_t spins) {
   if (!C || spins < 1 || spins > (1 << 20)) return fail(BCFMM_ERR_ARG, "debug_expire_wait: null context or spins not in 1..2^20");
   CU(launch_debug_expire_wait(C->err, spins, C->st));

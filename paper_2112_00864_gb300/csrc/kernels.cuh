@@ -67,6 +67,9 @@ cudaError_t launch_p2p_l2p_f64(const DevGeom& G, const DevTaskLists& L, const do
 cudaError_t launch_elem_sum(const DevGeom& G, const DevTaskLists& L, const double* phi, int64_t ntgt_pts,
                             const double* dens_src, int ndens, double* out, cudaStream_t st);
 
+// FP32 FMA throughput of the device (flop/s, 2 per FMA), CUDA events
+cudaError_t measure_ffma_rate(int device, double* flops);
+
 // FP64 direct evaluation of sampled target elements (out [ndens][n]);
 // src_rng [n][2]: sorted source point range of each target's mesh
 cudaError_t launch_direct_sample(const DevGeom& G, const DevTaskLists& L, const int64_t* targets, const int64_t* src_rng,

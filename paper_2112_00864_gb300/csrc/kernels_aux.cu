@@ -1,6 +1,8 @@
 // Auxiliary device passes: the FP64 direct evaluation of sampled target
 // elements (the discrete operator summed pair by pair, no expansions),
 // which the library uses to measure the error of a fast configuration.
+#include <algorithm>
+
 #include "kernels.cuh"
 
 namespace bcfmm {
@@ -64,6 +66,52 @@ cudaError_t launch_direct_sample(const DevGeom& G, const DevTaskLists& L, const 
   if (ndens < 1 || ndens > 16) return cudaErrorInvalidValue;
   k_direct_sample<<<n, kDirectThreads, 0, st>>>(G, L, targets, src_rng, dens, ndens, n, out);
   return cudaGetLastError();
+}
+
+// FP32 FMA throughput probe: every thread runs 8 independent FMA chains
+// (enough to cover the pipe latency) for `iters` steps; the result is
+// stored so that nothing is eliminated.
+__global__ void __launch_bounds__(256) k_ffma_rate(int iters, float a, float b, float* __restrict__ out) {
+  float x[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) x[i] = (float)(threadIdx.x + i);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = fmaf(x[i], a, b);
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) s += x[i];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+cudaError_t measure_ffma_rate(int device, double* flops) {
+  cudaDeviceProp prop;
+  cudaError_t e = cudaGetDeviceProperties(&prop, device);
+  if (e != cudaSuccess) return e;
+  const int blocks = prop.multiProcessorCount * 8, threads = 256, iters = 1 << 14;
+  float* out = nullptr;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  e = cudaMalloc(&out, sizeof(float) * blocks * threads);
+  if (e == cudaSuccess) e = cudaEventCreate(&t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&t1);
+  float best = 1e30f;
+  for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+    // a < 1 keeps the chains finite; rep 0 is the warm-up
+    k_ffma_rate<<<blocks, threads>>>(iters, 0.999f, 1e-3f, out);
+    e = cudaEventRecord(t0);
+    k_ffma_rate<<<blocks, threads>>>(iters, 0.999f, 1e-3f, out);
+    if (e == cudaSuccess) e = cudaEventRecord(t1);
+    if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+    if (e == cudaSuccess && rep > 0) best = std::min(best, ms);
+  }
+  if (e == cudaSuccess) *flops = 2.0 * 8.0 * iters * (double)blocks * threads / (best * 1e-3);
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  if (out) cudaFree(out);
+  return e;
 }
 
 }  // namespace bcfmm
