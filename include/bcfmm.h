@@ -65,14 +65,18 @@ typedef enum {
 typedef enum {
   BCFMM_FP64 = 0,          /* plain: every pass in FP64 on CUDA cores              */
   BCFMM_FP32 = 1,          /* P2P, P2M/M2M/L2L/L2P and M2L in FP32 (CUDA cores); M2L
-                              in the Taylor-coefficient form (FP32 products, FP64
-                              sums over list chunks)                              */
+                              in the Taylor-coefficient form (FP32 products,
+                              compensated sums over list chunks)                  */
   BCFMM_FP32_BF16X2 = 2,   /* FP32, M2L on tcgen05 tensor cores, BF16 hi+lo split
                               (hi*hi + hi*lo + lo*hi), FP32 accumulation in TMEM   */
   BCFMM_FP32_BF16X3 = 3    /* as above with a 3-term split (6 products)            */
 } bcfmm_precision;
 
-typedef enum { BCFMM_VOLUME = 0, BCFMM_BOUNDARY = 1 } bcfmm_density_kind;
+/* Densities: f of VtV/VtB (per tet), the single-layer density q = gamma_1 u
+ * of BtV (per triangle) and the double-layer density g = gamma_0 u of BtV
+ * (per triangle; contexts built with double_layer = 1).  BtV evaluates
+ * <phi_t, V~ q - K~ g> (Algorithm 3, Eq. green:ie:vol). */
+typedef enum { BCFMM_VOLUME = 0, BCFMM_BOUNDARY = 1, BCFMM_DIPOLE = 2 } bcfmm_density_kind;
 
 #define BCFMM_MAX_LEVELS 20   /* entries of bcfmm_params.p_level */
 
@@ -115,6 +119,14 @@ typedef struct {
                            p_level: q_l = min(p, q0 + L - l), L the deepest level of
                            the octree (over every mesh of a batch); 0 = use p_level;
                            0..12                                                    */
+  int32_t double_layer; /* 1: BtV also takes the double-layer density (BCFMM_DIPOLE):
+                           the build computes the FP64 near-rule corrections of the
+                           kernel dG/dn_y (closed-form solid angle of the source
+                           triangle, the composite rule of near_n / near_k over the
+                           target tet) for BtV's near pairs, whatever near_mode says
+                           for the single layer (near_mode 2: none).  Triangle
+                           normals follow the right-hand rule of tris (outward).
+                           0 = single layer only (default)                          */
 } bcfmm_params;
 
 /* Fills *prm with the defaults above.  Never fails. */
@@ -180,7 +192,11 @@ int bcfmm_build_like(const bcfmm_ctx* base, const bcfmm_params* prm, bcfmm_ctx**
 /*
  * Set the P0 density coefficients (one value per element, Sec. 1.2).
  *   kind   BCFMM_VOLUME: vals [ndens][ntet] (f of VtV/VtB);
- *          BCFMM_BOUNDARY: vals [ndens][ntri] (g of BtV)
+ *          BCFMM_BOUNDARY: vals [ndens][ntri] (single layer q of BtV);
+ *          BCFMM_DIPOLE: vals [ndens][ntri] (double layer g of BtV; the
+ *          context must be built with double_layer = 1; its ndens must
+ *          equal the single layer's when BtV runs; vals = NULL with
+ *          ndens = 0 removes it)
  *   vals   FP64; device memory if is_device != 0 (read on the context's
  *          stream before this call returns control of the buffer to the
  *          stream order), else host memory (copied synchronously)
@@ -202,6 +218,12 @@ int bcfmm_set_density(bcfmm_ctx* ctx, int32_t kind, const double* vals,
 int bcfmm_eval_vtv(bcfmm_ctx* ctx, double* out, int32_t out_is_device);
 int bcfmm_eval_vtb(bcfmm_ctx* ctx, double* out, int32_t out_is_device);
 int bcfmm_eval_btv(bcfmm_ctx* ctx, double* out, int32_t out_is_device);
+/* BtV output: <phi_t, V~ q> for the boundary density q, minus <phi_t, K~ g>
+ * when a double-layer density g is set (BCFMM_DIPOLE): the moments take
+ * <gamma_1 (y - c)^beta, g> (Algorithm 3), the near field dG/dn_y
+ * (FP32 or FP64 as the precision says) and the element sums the FP64
+ * double-layer corrections.  BCFMM_ERR_STATE: g set with a different
+ * ndens than q. */
 
 /*
  * Evaluate the tasks in task_mask (bit 0 VtV, bit 1 VtB, bit 2 BtV) as one
@@ -234,7 +256,9 @@ int bcfmm_eval_graph(bcfmm_ctx* ctx, int32_t task_mask, double* out_vtv, double*
  * deployment variant of the FP32 evaluation (precision BCFMM_FP32 or a
  * BF16 split).
  *   dens_dev  FP64 device array, one P0 value per source element (tets for
- *             VtV/VtB, triangles for BtV); read on the context's stream
+ *             VtV/VtB, triangles for BtV: the single layer only, a
+ *             double-layer density set on the context is not used);
+ *             read on the context's stream
  *   out_dev   FP64 device array, one value per target element; written
  *             asynchronously on the context's stream
  * The M2L keeps its partial sums (tensor cores: per work unit; Taylor

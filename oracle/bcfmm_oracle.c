@@ -9,7 +9,11 @@
  *
  * Kernel G(x,y) = 1/(4 pi |x-y|) (Sec. 1.1).  P0 (piecewise-constant)
  * Galerkin discretisation (Sec. 1.2): u_t = sum_s A_ts f_s with
- * A_ts = int_t int_s G.  The discrete operator the method approximates:
+ * A_ts = int_t int_s G.  Task 3 is the double-layer part of BtV
+ * (Algorithm 3, the term K~[gamma_0 u] of Eq. green:ie:vol): kernel
+ * dG/dn_y(x,y) = n_s.(x-y) / (4 pi |x-y|^3), n_s the unit normal of the
+ * source triangle by the right-hand rule (outward for the meshes used).
+ * The discrete operator the method approximates:
  *   far pairs  : product rule Q_ts = sum_i sum_j W_i W_j G(x_i, y_j)
  *                (4-point tet rule, 3-point triangle rule; the self point
  *                 x_i == y_j of a coincident pair is skipped)
@@ -108,6 +112,34 @@ double orc_tri_potential(const double *x, const double *v /*[3][3]*/) {
   double omega = 2.0 * atan2(num, den);
   acc -= fabs(w) * fabs(omega);
   return acc;
+}
+
+/* Double-layer potential of the flat triangle with unit density:
+ *   int_T n.(x-y)/|x-y|^3 ds_y = Omega(x),
+ * the solid angle T subtends at x, signed: positive when x lies on the side
+ * the normal n = (v1-v0) x (v2-v0) points to (for y in the plane,
+ * n.(x-y) is the height w of x).  Van Oosterom & Strackee give
+ * tan(Omega_u/2) = r1.(r2 x r3) / (l1 l2 l3 + (r1.r2) l3 + (r1.r3) l2 +
+ * (r2.r3) l1), r_i = v_i - x, l_i = |r_i|; for x at height w > 0 the
+ * triple product r1.(r2 x r3) = -w |(v1-v0) x (v2-v0)| is negative, so the
+ * signed angle is minus twice the atan2 of that quotient.  Over a closed
+ * outward-oriented surface the angles add up to -4 pi inside, 0 outside. */
+double orc_tri_solid_angle(const double *x, const double *v /*[3][3]*/) {
+  double r1[3], r2[3], r3[3], c23[3];
+  sub3(v, x, r1); sub3(v+3, x, r2); sub3(v+6, x, r3);
+  double l1 = norm3(r1), l2 = norm3(r2), l3 = norm3(r3);
+  cross3(r2, r3, c23);
+  double num = dot3(r1, c23);
+  double den = l1*l2*l3 + dot3(r1,r2)*l3 + dot3(r1,r3)*l2 + dot3(r2,r3)*l1;
+  return -2.0 * atan2(num, den);
+}
+
+/* unit normal of a triangle by the right-hand rule */
+void orc_tri_normal(const double *v, double *n) {
+  double a[3], b[3];
+  sub3(v+3, v, a); sub3(v+6, v, b); cross3(a, b, n);
+  double nn = norm3(n);
+  n[0] /= nn; n[1] /= nn; n[2] /= nn;
 }
 
 /* Potential of the uniform tetrahedron: psi(x) = int_tau dy/|x-y|.
@@ -242,16 +274,19 @@ static double tri_rule_apply(const double *v, int k, const orc_rule *R,
 
 static double fn_tet_pot(const double *x, const void *ctx) { return orc_tet_potential(x, (const double*)ctx); }
 static double fn_tri_pot(const double *x, const void *ctx) { return orc_tri_potential(x, (const double*)ctx); }
+static double fn_tri_dl(const double *x, const void *ctx) { return orc_tri_solid_angle(x, (const double*)ctx); }
 
 /* task: 0 = VtV (tet target, tet source), 1 = VtB (tri target, tet source),
- *       2 = BtV (tet target, tri source).  Returns N_ts (includes 1/(4 pi)). */
+ *       2 = BtV (tet target, tri source), 3 = BtV double layer (tet target,
+ *       tri source, kernel dG/dn_y).  Returns N_ts (includes 1/(4 pi)). */
 double orc_near_pair(int task, const double *tgt, const double *src,
                      const double *glx, const double *glw, int n, int k) {
   orc_rule R = { glx, glw, n, k };
   double s;
   if (task == 0)      s = tet_rule_apply(tgt, k, &R, fn_tet_pot, src);
   else if (task == 1) s = tri_rule_apply(tgt, k, &R, fn_tet_pot, src);
-  else                s = tet_rule_apply(tgt, k, &R, fn_tri_pot, src);
+  else if (task == 2) s = tet_rule_apply(tgt, k, &R, fn_tri_pot, src);
+  else                s = tet_rule_apply(tgt, k, &R, fn_tri_dl, src);
   return s / FOUR_PI;
 }
 
@@ -280,7 +315,7 @@ double orc_adaptive_pair(int task, const double *tgt, const double *src,
                          const double *glx, const double *glw, int n, double tol, int maxdepth) {
   orc_rule R = { glx, glw, n, 0 };
   if (task == 1) return NAN;  /* triangle targets: not needed by the pins */
-  double (*fn)(const double*, const void*) = (task == 0) ? fn_tet_pot : fn_tri_pot;
+  double (*fn)(const double*, const void*) = (task == 0) ? fn_tet_pot : (task == 2) ? fn_tri_pot : fn_tri_dl;
   double w0 = tet_rule_apply(tgt, 0, &R, fn, src);
   return adapt_tet(tgt, &R, fn, src, w0, tol, 0, maxdepth) / FOUR_PI;
 }
@@ -318,7 +353,7 @@ void orc_direct(int task, const double *tgt_el, int64_t ntgt, const double *src_
                 const double *dens, int ndens, const int64_t *targets, int64_t ntargets,
                 double eta_ns, const double *glx, const double *glw, int n, int k,
                 double *out, int nthreads) {
-  int nvt = (task == 1) ? 3 : 4, nvs = (task == 2) ? 3 : 4;
+  int nvt = (task == 1) ? 3 : 4, nvs = (task >= 2) ? 3 : 4;
   int nqt = (nvt == 4) ? 4 : 3, nqs = (nvs == 4) ? 4 : 3;
   double *sp = malloc(sizeof(double) * 3 * nqs * nsrc), *sw = malloc(sizeof(double) * nqs * nsrc);
   if (nvs == 4) orc_tet_quad(src_el, nsrc, sp, sw); else orc_tri_quad(src_el, nsrc, sp, sw);
@@ -339,12 +374,15 @@ void orc_direct(int task, const double *tgt_el, int64_t ntgt, const double *src_
       if (orc_is_near(tv, nvt, sv, nvs, eta_ns)) {
         a = orc_near_pair(task, tv, sv, glx, glw, n, k);
       } else {
+        double ns[3] = {0, 0, 0};
+        if (task == 3) orc_tri_normal(sv, ns);
         a = 0.0;
         for (int i = 0; i < nqt; ++i) for (int j = 0; j < nqs; ++j) {
           double d[3]; sub3(tp+3*i, sp+3*(nqs*s+j), d);
           double r = norm3(d);
           if (r == 0.0) continue;
-          a += tw[i] * sw[nqs*s+j] / (FOUR_PI * r);
+          if (task == 3) a += tw[i] * sw[nqs*s+j] * dot3(ns, d) / (FOUR_PI * r * r * r);
+          else           a += tw[i] * sw[nqs*s+j] / (FOUR_PI * r);
         }
       }
       for (int q = 0; q < ndens; ++q) acc[q] += a * dens[(int64_t)q*nsrc + s];

@@ -46,6 +46,7 @@ void orc_tri_quad(const double *tris, int64_t ntri, double *pts, double *wts);
 double orc_near_pair(int task, const double *tgt, const double *src,
                      const double *glx, const double *glw, int n, int k);
 int orc_is_near(const double *tv, int ntv, const double *sv, int nsv, double eta_ns);
+void orc_tri_normal(const double *v, double *n);
 
 /* ------------------------------------------------------------------ */
 /* multi-indices                                                        */
@@ -317,7 +318,10 @@ static int neighbour_offsets(double eta0, int (*off)[3], int cap) {
 /* O2 driver                                                            */
 /* ------------------------------------------------------------------ */
 /* task 0 VtV (sources/targets: tet points), 1 VtB (sources tet, targets tri),
- * 2 BtV (sources tri, targets tet).  dens: [ndens][nsrc elements].
+ * 2 BtV (sources tri, targets tet), 3 BtV double layer K~ (sources tri with
+ * their unit normals n, targets tet; Algorithm 3: the moment of a source
+ * point is <gamma_1 (y - c)^beta, g> = w g n . grad_y (y - c)^beta, the near
+ * field uses dG/dn_y).  dens: [ndens][nsrc elements].
  * targets: requested target elements; out[ndens][ntargets].
  * stats (optional, int64[8]): nbox, nleaf, maxlevel, n_m2l, n_p2p, 0,0,0.
  * qlev (optional, int[20]): expansion order q_l of level l (Sec. 3.3 uses
@@ -356,7 +360,7 @@ int orc_fmm(int task, const double *tets, int64_t ntet, const double *tris, int6
   int (*NB)[3] = malloc(sizeof(int[3]) * noff_cap);
   int nnb = neighbour_offsets(eta0, NB, noff_cap);
 
-  int src_is_v = (task != 2), tgt_is_v = (task != 1);
+  int src_is_v = (task != 2 && task != 3), tgt_is_v = (task != 1), dl = (task == 3);
   const double *SP = src_is_v ? VP : BP, *SW = src_is_v ? VW : BW;
   const double *TP = tgt_is_v ? VP : BP, *TW = tgt_is_v ? VW : BW;
   const int64_t *sperm = src_is_v ? T.pv : T.pb, *tperm = tgt_is_v ? T.pv : T.pb;
@@ -372,6 +376,9 @@ int orc_fmm(int task, const double *tets, int64_t ntet, const double *tris, int6
   double *SWd = malloc(sizeof(double) * ndens * (nsp + 1));
   for (int d = 0; d < ndens; ++d)
     for (int64_t j = 0; j < nsp; ++j) SWd[(int64_t)d*nsp + j] = SW[j] * dens[(int64_t)d*nsrc_el + j/nqs];
+  /* double layer: unit normal of each source triangle */
+  double *SN = calloc(3 * (size_t)(nsrc_el + 1), sizeof(double));
+  if (dl) for (int64_t e = 0; e < nsrc_el; ++e) orc_tri_normal(tris + 9*e, SN + 3*e);
   double *mom = calloc((size_t)T.n * ndens * np, sizeof(double));
   double *loc = calloc((size_t)T.n * ndens * np, sizeof(double));
   double *phi = calloc((size_t)ndens * (ntp + 1), sizeof(double));
@@ -387,7 +394,18 @@ int orc_fmm(int task, const double *tets, int64_t ntet, const double *tris, int6
       int64_t j = sperm[q];
       double dx[3] = { SP[3*j]-B->c[0], SP[3*j+1]-B->c[1], SP[3*j+2]-B->c[2] };
       for (int c = 0; c < np; ++c) {
-        double mono = ipow(dx[0], M.mi[c][0]) * ipow(dx[1], M.mi[c][1]) * ipow(dx[2], M.mi[c][2]);
+        const int *be = M.mi[c];
+        double mono;
+        if (!dl) {
+          mono = ipow(dx[0], be[0]) * ipow(dx[1], be[1]) * ipow(dx[2], be[2]);
+        } else {
+          /* n . grad (y - c)^beta = sum_i n_i beta_i (y - c)^(beta - e_i) */
+          const double *nn = SN + 3*(j/nqs);
+          mono = 0.0;
+          if (be[0]) mono += nn[0] * be[0] * ipow(dx[0], be[0]-1) * ipow(dx[1], be[1]) * ipow(dx[2], be[2]);
+          if (be[1]) mono += nn[1] * be[1] * ipow(dx[0], be[0]) * ipow(dx[1], be[1]-1) * ipow(dx[2], be[2]);
+          if (be[2]) mono += nn[2] * be[2] * ipow(dx[0], be[0]) * ipow(dx[1], be[1]) * ipow(dx[2], be[2]-1);
+        }
         for (int d = 0; d < ndens; ++d) mom[((size_t)bi*ndens + d)*np + c] += SWd[(int64_t)d*nsp + j] * mono;
       }
     }
@@ -483,7 +501,12 @@ int orc_fmm(int task, const double *tets, int64_t ntet, const double *tris, int6
             double dd[3] = { x[0]-SP[3*j], x[1]-SP[3*j+1], x[2]-SP[3*j+2] };
             double rr = sqrt(dd[0]*dd[0] + dd[1]*dd[1] + dd[2]*dd[2]);
             if (rr == 0.0) continue;
-            s += SWd[(int64_t)d*nsp + j] / (FOUR_PI * rr);
+            if (dl) {
+              const double *nn = SN + 3*(j/nqs);
+              s += SWd[(int64_t)d*nsp + j] * (nn[0]*dd[0] + nn[1]*dd[1] + nn[2]*dd[2]) / (FOUR_PI * rr * rr * rr);
+            } else {
+              s += SWd[(int64_t)d*nsp + j] / (FOUR_PI * rr);
+            }
           }
         s += orc_l2p(loc + ((size_t)bi*ndens + d)*np, B->c, p, x);
         phi[(int64_t)d*ntp + i] = s;
@@ -515,7 +538,12 @@ int orc_fmm(int task, const double *tets, int64_t ntet, const double *tris, int6
         double dd[3] = { x[0]-y[0], x[1]-y[1], x[2]-y[2] };
         double rr = sqrt(dd[0]*dd[0] + dd[1]*dd[1] + dd[2]*dd[2]);
         if (rr == 0.0) continue;
-        q += TW[nqt*t + i] * SW[nqs*s + j] / (FOUR_PI * rr);
+        if (dl) {
+          const double *nn = SN + 3*s;
+          q += TW[nqt*t + i] * SW[nqs*s + j] * (nn[0]*dd[0] + nn[1]*dd[1] + nn[2]*dd[2]) / (FOUR_PI * rr * rr * rr);
+        } else {
+          q += TW[nqt*t + i] * SW[nqs*s + j] / (FOUR_PI * rr);
+        }
       }
       for (int d = 0; d < ndens; ++d) out[(int64_t)d*ntargets + ti] += (a - q) * dens[(int64_t)d*nsrc_el + s];
     }
@@ -527,7 +555,7 @@ int orc_fmm(int task, const double *tets, int64_t ntet, const double *tris, int6
     stats[0] = T.n; stats[1] = nleaf; stats[2] = maxl; stats[3] = n_m2l; stats[4] = n_p2p;
     stats[5] = stats[6] = stats[7] = 0;
   }
-  free(VP); free(VW); free(BP); free(BW); free(SWd); free(mom); free(loc); free(phi);
+  free(VP); free(VW); free(BP); free(BW); free(SWd); free(SN); free(mom); free(loc); free(phi);
   midx_free(&M); free_tree(&T); free(NB);
   return 0;
 }

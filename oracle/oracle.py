@@ -19,7 +19,10 @@ _LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
 _lib = None
 _lock = threading.Lock()
 
-TASKS = {"vtv": 0, "vtb": 1, "btv": 2}
+# btv_dl: the double-layer part K~[gamma_0 u] of BtV (Algorithm 3, Eq.
+# green:ie:vol), tet targets, triangle sources with their right-hand-rule
+# normals; the BtV of Algorithm 3 is btv(gamma_1 u) - btv_dl(gamma_0 u)
+TASKS = {"vtv": 0, "vtb": 1, "btv": 2, "btv_dl": 3}
 
 # defaults of the discrete operator (shared by convention with the library)
 ETA_NS = 1.0 - 2.0 ** -20      # near iff eta > ETA_NS: every touching pair (eta >= 1) is near
@@ -54,6 +57,8 @@ def lib():
             L.orc_tri_potential.argtypes = [p, p]
             L.orc_tet_potential.restype = d
             L.orc_tet_potential.argtypes = [p, p]
+            L.orc_tri_solid_angle.restype = d
+            L.orc_tri_solid_angle.argtypes = [p, p]
             L.orc_near_pair.restype = d
             L.orc_near_pair.argtypes = [i, p, p, p, p, i, i]
             L.orc_adaptive_pair.restype = d
@@ -112,6 +117,12 @@ def tri_potential(x, tri) -> float:
     return lib().orc_tri_potential(_ptr(_f64(x)), _ptr(_f64(tri)))
 
 
+def tri_solid_angle(x, tri) -> float:
+    """int_T n.(x - y)/|x - y|^3 ds_y: the signed solid angle (closed form),
+    positive on the side of the right-hand-rule normal."""
+    return lib().orc_tri_solid_angle(_ptr(_f64(x)), _ptr(_f64(tri)))
+
+
 def tet_potential(x, tet) -> float:
     """int_tau dy / |x - y| (closed form via the faces)."""
     return lib().orc_tet_potential(_ptr(_f64(x)), _ptr(_f64(tet)))
@@ -156,7 +167,7 @@ def _task_arrays(task, mesh):
     tets = _f64(mesh.verts[mesh.tets])
     tris = _f64(mesh.verts[mesh.tris])
     tgt = tris if task == "vtb" else tets
-    src = tris if task == "btv" else tets
+    src = tris if task in ("btv", "btv_dl") else tets
     return tets, tris, tgt, src
 
 

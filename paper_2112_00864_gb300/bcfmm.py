@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libbcfmm.so")
 BCFMM_OK = 0
 STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_MESH", -3: "ERR_CUDA", -4: "ERR_OOM", -5: "ERR_TIMEOUT", -6: "ERR_STATE"}
 PRECISION = {"fp64": 0, "fp32": 1, "bf16x2": 2, "bf16x3": 3}
-VOLUME, BOUNDARY = 0, 1
+VOLUME, BOUNDARY, DIPOLE = 0, 1, 2
 EXPORTED = ["bcfmm_default_params", "bcfmm_build_bc_tree", "bcfmm_set_density", "bcfmm_eval_vtv",
             "bcfmm_eval_vtb", "bcfmm_eval_btv", "bcfmm_stats", "bcfmm_last_error", "bcfmm_destroy",
             "bcfmm_debug_m2l_matrix", "bcfmm_eval_noalloc", "bcfmm_build_batch", "bcfmm_eval_graph",
@@ -35,7 +35,8 @@ class Params(C.Structure):
     _fields_ = [("p", C.c_int32), ("leaf_size", C.c_int32), ("eta_ns", C.c_double), ("near_n", C.c_int32),
                 ("near_k", C.c_int32), ("precision", C.c_int32), ("timing", C.c_int32), ("eta0", C.c_double),
                 ("tc_unit", C.c_int32), ("near_mode", C.c_int32), ("mlp_tol", C.c_double), ("mlp_blob", C.c_void_p),
-                ("mlp_blob_bytes", C.c_int64), ("p_level", C.c_int32 * 20), ("q0", C.c_int32)]
+                ("mlp_blob_bytes", C.c_int64), ("p_level", C.c_int32 * 20), ("q0", C.c_int32),
+                ("double_layer", C.c_int32)]
 
 
 class BcfmmError(RuntimeError):
@@ -227,7 +228,7 @@ class Context:
                                                self.tri_off.ctypes.data, self.nmesh, C.byref(self.params),
                                                C.c_void_p(handle), C.byref(ctx)))
         self._ctx = ctx
-        self.ndens = {VOLUME: 0, BOUNDARY: 0}
+        self.ndens = {VOLUME: 0, BOUNDARY: 0, DIPOLE: 0}
 
     @classmethod
     def from_meshes(cls, meshes, **kw):
@@ -261,7 +262,7 @@ class Context:
         new._ctx = None
         _check(self._lib.bcfmm_build_like(self._ctx, C.byref(prm), C.byref(ctx)))
         new._ctx = ctx
-        new.ndens = {VOLUME: 0, BOUNDARY: 0}
+        new.ndens = {VOLUME: 0, BOUNDARY: 0, DIPOLE: 0}
         return new
 
     def direct_sample(self, task: str, targets) -> np.ndarray:
@@ -315,10 +316,19 @@ class Context:
             vals = vals.contiguous()
             assert vals.dtype.is_floating_point and vals.element_size() == 8, "densities must be float64"
             nd = vals.shape[0]
-        self._dens_keep = vals
+        if not hasattr(self, "_keep"):
+            self._keep = {}
+        self._keep[kind] = vals
         ptr, dev = _ptr(vals)
         _check(self._lib.bcfmm_set_density(self._ctx, kind, C.c_void_p(ptr), nd, dev))
         self.ndens[kind] = nd
+
+    def clear_dipole(self):
+        """Remove the double-layer density (BtV then evaluates V~ q alone)."""
+        _check(self._lib.bcfmm_set_density(self._ctx, DIPOLE, None, 0, 0))
+        self.ndens[DIPOLE] = 0
+        if hasattr(self, "_keep"):
+            self._keep.pop(DIPOLE, None)
 
     def _eval(self, fn, nel: int, kind: int, out=None):
         nd = self.ndens[kind]

@@ -108,8 +108,9 @@ struct bcfmm_ctx {
   bool mlp_has[3] = {false, false, false};
   std::vector<float> mlp_params[3], mlp_eps[3];
   // densities
-  int ndens[2] = {0, 0}, ndp[2] = {0, 0};
-  double* dens[2] = {nullptr, nullptr};
+  // densities: [BCFMM_VOLUME], [BCFMM_BOUNDARY], [BCFMM_DIPOLE]
+  int ndens[3] = {0, 0, 0}, ndp[3] = {0, 0, 0};
+  double* dens[3] = {nullptr, nullptr, nullptr};
   int* err = nullptr;                  // device error word (bounded device waits)
   size_t tc_partial_per_dens = 0;      // largest tensor-core partial-sum need over the tasks (float2)
   // Taylor-form M2L (BCFMM_FP32): offset coefficients, prescaled moments,
@@ -124,6 +125,8 @@ struct bcfmm_ctx {
   int work_ndp = 0;
   double *W64 = nullptr, *mom64 = nullptr, *loc64 = nullptr, *phi = nullptr, *out_dev = nullptr;
   float *W32 = nullptr, *mom32 = nullptr, *loc32 = nullptr;
+  double* W64dl = nullptr;               // BtV double-layer point weights w g (double_layer)
+  float* W32dl = nullptr;
   // stats
   int nmesh = 1;
   std::vector<int64_t> mesh_tet_off, mesh_tri_off;
@@ -142,7 +145,7 @@ struct bcfmm_ctx {
   // CUDA graph of bcfmm_eval_graph
   struct {
     cudaGraphExec_t exec = nullptr;
-    int mask = 0, work_gen = -1, ndens[2] = {0, 0};
+    int mask = 0, work_gen = -1, ndens[3] = {0, 0, 0};
     double* out[3] = {nullptr, nullptr, nullptr};
     int nodes = 0;
   } graph;
@@ -185,6 +188,7 @@ extern "C" void bcfmm_default_params(bcfmm_params* prm) {
   prm->mlp_blob_bytes = 0;
   for (int l = 0; l < BCFMM_MAX_LEVELS; ++l) prm->p_level[l] = 0;
   prm->q0 = 0;
+  prm->double_layer = 0;
 }
 
 extern "C" const char* bcfmm_last_error(void) { return g_err.c_str(); }
@@ -475,6 +479,43 @@ static int upload_task(bcfmm_ctx* C, const HostSetup& H, int t) {
     if (par) m.release(par);
   }
   }
+  // BtV double layer: FP64 near-rule corrections of dG/dn_y on the same
+  // near-pair CSR (closed-form solid angle inside the composite rule)
+  L.cor_val_dl = nullptr;
+  if (t == 2 && C->prm.double_layer) {
+    double* cdl;
+    CU(m.alloc(&cdl, std::max<int64_t>(D.nnz, 1)));
+    if (D.nnz == 0) {
+    } else if (C->reuse) {
+      CU(cudaMemcpyAsync(cdl, C->reuse->task[2].L.cor_val_dl, D.nnz * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    } else if (C->prm.near_mode == 2) {
+      CU(cudaMemsetAsync(cdl, 0, D.nnz * sizeof(double), st));
+    } else {
+      std::vector<int> row(T.cor_col.size());
+      for (int64_t e = 0; e < nte; ++e)
+        for (int64_t k = T.cor_off[e]; k < T.cor_off[e + 1]; ++k) row[k] = (int)e;
+      double *tv, *sv, *tqp, *tqw, *sqp, *sqw, *glx, *glw;
+      int* drow;
+      CU(m.upload(&drow, row.data(), row.size(), st));
+      CU(m.upload(&tv, H.tet_v.data(), H.tet_v.size(), st));
+      CU(m.upload(&sv, H.tri_v.data(), H.tri_v.size(), st));
+      CU(m.upload(&tqp, H.qp[0].data(), H.qp[0].size(), st));
+      CU(m.upload(&tqw, H.qw[0].data(), H.qw[0].size(), st));
+      CU(m.upload(&sqp, H.qp[1].data(), H.qp[1].size(), st));
+      CU(m.upload(&sqw, H.qw[1].data(), H.qw[1].size(), st));
+      std::vector<double> gx, gw;
+      gauss_legendre01(C->prm.near_n, gx, gw);
+      CU(m.upload(&glx, gx.data(), gx.size(), st));
+      CU(m.upload(&glw, gw.data(), gw.size(), st));
+      CU(launch_near_rule(3, D.nnz, nullptr, drow, L.cor_col, tv, sv, tqp, tqw, sqp, sqw, glx, glw, C->prm.near_n,
+                          C->prm.near_k, 0, cdl, st));
+      CU(cudaStreamSynchronize(st));
+      for (void* p : {(void*)tv, (void*)sv, (void*)tqp, (void*)tqw, (void*)sqp, (void*)sqw, (void*)glx, (void*)glw,
+                      (void*)drow})
+        m.release(p);
+    }
+    L.cor_val_dl = cdl;
+  }
   // counts for the statistics and the roofline
   D.near_boxes = (int64_t)T.near_box.size();
   D.m2l_pairs = (int64_t)T.vl_src.size();
@@ -575,6 +616,7 @@ static int build_impl(const double* verts, const int64_t* vert_off, const int32_
   const bool tc_mode = prm.precision == BCFMM_FP32_BF16X2 || prm.precision == BCFMM_FP32_BF16X3;
   const int nsplit = prm.precision == BCFMM_FP32_BF16X3 ? 3 : 2;
   if (prm.q0 < 0 || prm.q0 > kMaxP) return fail(BCFMM_ERR_ARG, "build: q0 must be in 0..12");
+  if (prm.double_layer != 0 && prm.double_layer != 1) return fail(BCFMM_ERR_ARG, "build: double_layer must be 0 or 1");
 
   // host phase per mesh; meshes of a batch in parallel, largest first
   const double th = wall();
@@ -730,6 +772,22 @@ static int build_impl(const double* verts, const int64_t* vert_off, const int32_
               m.upload(&dl, lo.data(), n, st) == cudaSuccess && m.upload(&de, el.data(), n, st) == cudaSuccess;
     if (!ok) return cleanup(fail(BCFMM_ERR_OOM, "build: device allocation failed (points)"));
     G.pt64[c] = dp; G.pthi[c] = dh; G.ptlo[c] = dl; G.pt_elem[c] = de;
+  }
+  // unit normal of every triangle (right-hand rule of its vertex order)
+  {
+    const int64_t nf = (int64_t)(H.tri_v.size() / 9);
+    std::vector<double4_32a> nrm(std::max<int64_t>(nf, 1), make_double4_32a(0, 0, 0, 0));
+    for (int64_t f = 0; f < nf; ++f) {
+      const double* v = &H.tri_v[9 * f];
+      const double a[3] = {v[3] - v[0], v[4] - v[1], v[5] - v[2]}, b[3] = {v[6] - v[0], v[7] - v[1], v[8] - v[2]};
+      double n[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+      const double nn = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+      nrm[f] = make_double4_32a(n[0] / nn, n[1] / nn, n[2] / nn, 0.0);
+    }
+    double4_32a* dn;
+    if (m.upload(&dn, nrm.data(), nrm.size(), st) != cudaSuccess)
+      return cleanup(fail(BCFMM_ERR_OOM, "build: device allocation failed (normals)"));
+    G.tri_nrm = dn;
   }
   // translation tables: M2L transposed per offset code, M2M / L2L per octant
   {
@@ -1128,8 +1186,9 @@ extern "C" int bcfmm_build_like(const bcfmm_ctx* base, const bcfmm_params* prm, 
   if (out) *out = nullptr;
   if (!base || !prm || !out) return fail(BCFMM_ERR_ARG, "build_like: null argument");
   if (prm->eta_ns != base->prm.eta_ns || prm->near_n != base->prm.near_n || prm->near_k != base->prm.near_k ||
-      prm->near_mode != base->prm.near_mode)
-    return fail(BCFMM_ERR_ARG, "build_like: eta_ns, near_n, near_k and near_mode must match the base context");
+      prm->near_mode != base->prm.near_mode || prm->double_layer != base->prm.double_layer)
+    return fail(BCFMM_ERR_ARG,
+                "build_like: eta_ns, near_n, near_k, near_mode and double_layer must match the base context");
   int dev = -1;
   CU(cudaGetDevice(&dev));
   if (dev != base->device) return fail(BCFMM_ERR_STATE, "build_like: the base context's device is not current");
@@ -1149,8 +1208,10 @@ static int ensure_work(bcfmm_ctx* C, int ndp) {
   auto& m = C->mem;
   for (void* p : {(void*)C->W64, (void*)C->mom64, (void*)C->loc64, (void*)C->phi, (void*)C->out_dev, (void*)C->W32,
                   (void*)C->mom32, (void*)C->loc32, (void*)C->tc_partial, (void*)C->tc_momb, (void*)C->ty_momp,
-                  (void*)C->ty_partial})
+                  (void*)C->ty_partial, (void*)C->W64dl, (void*)C->W32dl})
     if (p) m.release(p);
+  C->W64dl = nullptr;
+  C->W32dl = nullptr;
   C->tc_partial = nullptr;
   C->tc_momb = nullptr;
   C->ty_momp = C->ty_partial = nullptr;
@@ -1160,6 +1221,10 @@ static int ensure_work(bcfmm_ctx* C, int ndp) {
   const bool f64 = C->prm.precision == BCFMM_FP64;
   CU(m.alloc(&C->phi, (size_t)ndp * npmax));
   CU(m.alloc(&C->out_dev, (size_t)ndp * nel));
+  if (C->prm.double_layer && C->npts[1] > 0) {
+    if (f64) CU(m.alloc(&C->W64dl, (size_t)ndp * C->npts[1]));
+    else CU(m.alloc(&C->W32dl, (size_t)ndp * C->npts[1]));
+  }
   if (f64) {
     CU(m.alloc(&C->W64, (size_t)ndp * npmax));
     CU(m.alloc(&C->mom64, nexp));
@@ -1187,8 +1252,15 @@ static int ensure_work(bcfmm_ctx* C, int ndp) {
 }
 
 extern "C" int bcfmm_set_density(bcfmm_ctx* C, int32_t kind, const double* vals, int32_t ndens, int32_t is_device) {
+  if (C && kind == BCFMM_DIPOLE && !vals && ndens == 0) {
+    C->ndens[kind] = C->ndp[kind] = 0;     // remove the double-layer density
+    return BCFMM_OK;
+  }
   if (!C || !vals) return fail(BCFMM_ERR_ARG, "set_density: null argument");
-  if (kind != BCFMM_VOLUME && kind != BCFMM_BOUNDARY) return fail(BCFMM_ERR_ARG, "set_density: unknown kind");
+  if (kind != BCFMM_VOLUME && kind != BCFMM_BOUNDARY && kind != BCFMM_DIPOLE)
+    return fail(BCFMM_ERR_ARG, "set_density: unknown kind");
+  if (kind == BCFMM_DIPOLE && !C->prm.double_layer)
+    return fail(BCFMM_ERR_STATE, "set_density: double-layer density needs a context built with double_layer = 1");
   if (ndens < 1 || ndens > 16) return fail(BCFMM_ERR_ARG, "set_density: ndens must be in 1..16");
   const int64_t nel = kind == BCFMM_VOLUME ? C->ntet : C->ntri;
   if (nel == 0) return fail(BCFMM_ERR_ARG, "set_density: the mesh has no elements of this kind");
@@ -1224,6 +1296,10 @@ static int eval_impl(bcfmm_ctx* C, int t, double* out, int out_is_device, bool s
     return fail(BCFMM_ERR_STATE, kind == 0 ? "eval: volume density not set" : "eval: boundary density not set");
   if (!out) return fail(BCFMM_ERR_ARG, "eval: null output");
   const int ndens = C->ndens[kind], ndp = C->ndp[kind];
+  // BtV with a double-layer density g: V~ q - K~ g (Algorithm 3)
+  const bool dl = t == 2 && C->ndens[BCFMM_DIPOLE] > 0;
+  if (dl && C->ndens[BCFMM_DIPOLE] != ndens)
+    return fail(BCFMM_ERR_STATE, "eval: the double-layer density's ndens differs from the boundary density's");
   const int rc = ensure_work(C, ndp);
   if (rc != BCFMM_OK) return rc;
   cudaStream_t st = C->st;
@@ -1240,12 +1316,14 @@ static int eval_impl(bcfmm_ctx* C, int t, double* out, int out_is_device, bool s
   if (f64) {
     if (!skip_up) {
       CU(launch_weights<double>(G, L.src_cls, nsp, C->dens[kind], nsel, ndens, ndp, C->W64, st));
+      if (dl) CU(launch_weights<double>(G, 1, nsp, C->dens[BCFMM_DIPOLE], nsel, ndens, ndp, C->W64dl, st));
       CU(cudaMemsetAsync(C->mom64, 0, nexp * sizeof(double), st));
     }
     if (!skip_far) CU(cudaMemsetAsync(C->loc64, 0, nexp * sizeof(double), st));
     if (tm) CU(cudaEventRecord(ev[1], st));
     if (!skip_up) {
       CU(launch_p2m<double>(G, L, C->W64, nsp, ndp, C->mom64, st));
+      if (dl) CU(launch_p2m_dl<double>(G, L, C->W64dl, nsp, ndp, C->mom64, st));
       for (int l = C->nlevels - 1; l >= 0; --l) {
         const int n = D.m2m_off[l + 1] - D.m2m_off[l];
         CU(launch_m2m<double>(G, D.m2m_parent + D.m2m_off[l], n, C->M2M64, ndp, C->mom64, st));
@@ -1260,15 +1338,18 @@ static int eval_impl(bcfmm_ctx* C, int t, double* out, int out_is_device, bool s
     }
     if (tm) CU(cudaEventRecord(ev[4], st));
     CU(launch_p2p_l2p_f64(G, L, C->W64, nsp, ntp, ndp, C->loc64, C->phi, st));
+    if (dl) CU(launch_p2p_dl<double>(G, L, C->W64dl, nsp, ntp, ndp, C->phi, st));
   } else {
     if (!skip_up) {
       CU(launch_weights<float>(G, L.src_cls, nsp, C->dens[kind], nsel, ndens, ndp, C->W32, st));
+      if (dl) CU(launch_weights<float>(G, 1, nsp, C->dens[BCFMM_DIPOLE], nsel, ndens, ndp, C->W32dl, st));
       CU(cudaMemsetAsync(C->mom32, 0, nexp * sizeof(float), st));
     }
     if (!skip_far) CU(cudaMemsetAsync(C->loc32, 0, nexp * sizeof(float), st));
     if (tm) CU(cudaEventRecord(ev[1], st));
     if (!skip_up) {
       CU(launch_p2m<float>(G, L, C->W32, nsp, ndp, C->mom32, st));
+      if (dl) CU(launch_p2m_dl<float>(G, L, C->W32dl, nsp, ndp, C->mom32, st));
       for (int l = C->nlevels - 1; l >= 0; --l) {
         const int n = D.m2m_off[l + 1] - D.m2m_off[l];
         CU(launch_m2m<float>(G, D.m2m_parent + D.m2m_off[l], n, C->M2M32, ndp, C->mom32, st));
@@ -1292,9 +1373,10 @@ static int eval_impl(bcfmm_ctx* C, int t, double* out, int out_is_device, bool s
     }
     if (tm) CU(cudaEventRecord(ev[4], st));
     CU(launch_p2p_l2p_f32(G, L, C->W32, nsp, ntp, ndp, C->loc32, C->phi, st));
+    if (dl) CU(launch_p2p_dl<float>(G, L, C->W32dl, nsp, ntp, ndp, C->phi, st));
   }
   if (tm) CU(cudaEventRecord(ev[5], st));
-  CU(launch_elem_sum(G, L, C->phi, ntp, C->dens[kind], ndens, outd, st));
+  CU(launch_elem_sum(G, L, C->phi, ntp, C->dens[kind], ndens, outd, st, dl ? C->dens[BCFMM_DIPOLE] : nullptr));
   if (tm) CU(cudaEventRecord(ev[6], st));
   if (!out_is_device) {
     CU(cudaMemcpyAsync(out, C->out_dev, (size_t)ndens * L.ntgt_el * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -1335,7 +1417,7 @@ extern "C" int bcfmm_eval_graph(bcfmm_ctx* C, int32_t mask, double* out_vtv, dou
   }
   auto& g = C->graph;
   const bool same = g.exec && g.mask == mask && g.work_gen == C->work_gen && g.ndens[0] == C->ndens[0] &&
-                    g.ndens[1] == C->ndens[1] && std::equal(outs, outs + 3, g.out);
+                    g.ndens[1] == C->ndens[1] && g.ndens[2] == C->ndens[2] && std::equal(outs, outs + 3, g.out);
   if (!same) {
     if (g.exec) { cudaGraphExecDestroy(g.exec); g.exec = nullptr; }
     if (!C->cap_st) CU(cudaStreamCreateWithFlags(&C->cap_st, cudaStreamNonBlocking));
@@ -1372,6 +1454,7 @@ extern "C" int bcfmm_eval_graph(bcfmm_ctx* C, int32_t mask, double* out_vtv, dou
     g.work_gen = C->work_gen;
     g.ndens[0] = C->ndens[0];
     g.ndens[1] = C->ndens[1];
+    g.ndens[2] = C->ndens[2];
     std::copy(outs, outs + 3, g.out);
     g.nodes = nkernel;
   }

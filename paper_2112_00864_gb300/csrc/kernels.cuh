@@ -25,6 +25,7 @@ struct DevGeom {
   const float4* pthi[2];         // float hi parts (x, y, z, weight)
   const float4* ptlo[2];         // float lo parts (x - hi, ...)
   const int* pt_elem[2];         // sorted point -> element
+  const double4_32a* tri_nrm;    // unit normal of each triangle (right-hand rule; w unused)
 };
 
 struct DevTaskLists {
@@ -35,6 +36,7 @@ struct DevTaskLists {
   int n_l2p; const int* l2p_leaf;
   int64_t ntgt_el, nsrc_el;
   const int64_t* cor_off; const int* cor_col; const double* cor_val;
+  const double* cor_val_dl;      // BtV: near-rule corrections of dG/dn_y (same CSR), or null
   const int* elem_pts;           // [ntgt_el][4] sorted positions of the element's points (-1 pad)
   int nq_tgt;                    // 4 (tets) or 3 (triangles)
   int src_cls, tgt_cls;
@@ -64,8 +66,18 @@ cudaError_t launch_p2p_l2p_f32(const DevGeom& G, const DevTaskLists& L, const fl
                                int64_t ntgt_pts, int ndp, const float* loc, double* phi, cudaStream_t st);
 cudaError_t launch_p2p_l2p_f64(const DevGeom& G, const DevTaskLists& L, const double* W, int64_t nsrc_pts,
                                int64_t ntgt_pts, int ndp, const double* loc, double* phi, cudaStream_t st);
+// dens_dl: BtV double-layer density (subtracts its corrections L.cor_val_dl), or null
 cudaError_t launch_elem_sum(const DevGeom& G, const DevTaskLists& L, const double* phi, int64_t ntgt_pts,
-                            const double* dens_src, int ndens, double* out, cudaStream_t st);
+                            const double* dens_src, int ndens, double* out, cudaStream_t st,
+                            const double* dens_dl = nullptr);
+// BtV double layer (Algorithm 3): moments -<gamma_1 (y-c)^b, g> added to mom,
+// near field -sum Wg n.(x-y)/(4 pi r^3) subtracted from phi
+template <typename T>
+cudaError_t launch_p2m_dl(const DevGeom& G, const DevTaskLists& L, const T* W, int64_t nsrc_pts, int ndp, T* mom,
+                          cudaStream_t st);
+template <typename T>
+cudaError_t launch_p2p_dl(const DevGeom& G, const DevTaskLists& L, const T* W, int64_t nsrc_pts, int64_t ntgt_pts,
+                          int ndp, double* phi, cudaStream_t st);
 
 // FP32 FMA throughput of the device (flop/s, 2 per FMA), CUDA events
 cudaError_t measure_ffma_rate(int device, double* flops);
@@ -75,7 +87,8 @@ cudaError_t measure_ffma_rate(int device, double* flops);
 cudaError_t launch_direct_sample(const DevGeom& G, const DevTaskLists& L, const int64_t* targets, const int64_t* src_rng,
                                  int n, const double* dens, int ndens, double* out, cudaStream_t st);
 
-// setup: near-rule corrections C_ts = N_ts - Q_ts (FP64)
+// setup: near-rule corrections C_ts = N_ts - Q_ts (FP64); task 0 VtV,
+// 1 VtB, 2 BtV single layer, 3 BtV double layer (kernel dG/dn_y)
 // (sel: optional list of CSR positions; nnz is then its length)
 cudaError_t launch_near_rule(int task, int64_t nnz, const int64_t* sel, const int* row, const int* col,
                              const double* tgt_v, const double* src_v,

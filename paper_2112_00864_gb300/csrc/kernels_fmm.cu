@@ -758,7 +758,8 @@ cudaError_t launch_p2p_l2p_f64(const DevGeom& G, const DevTaskLists& L, const do
 // One warp per target element: u[d][e] = sum_q w_q phi[d][pos_q]
 //                                      + sum_k C[k] dens[d][col[k]].
 __global__ void k_elem_sum(DevGeom G, DevTaskLists L, const double* __restrict__ phi, int64_t ntp,
-                           const double* __restrict__ dens, int ndens, double* __restrict__ out) {
+                           const double* __restrict__ dens, int ndens, const double* __restrict__ dens_dl,
+                           double* __restrict__ out) {
   const int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (e >= L.ntgt_el) return;
@@ -771,6 +772,9 @@ __global__ void k_elem_sum(DevGeom G, DevTaskLists L, const double* __restrict__
     }
     const int64_t k0 = L.cor_off[e], k1 = L.cor_off[e + 1];
     for (int64_t k = k0 + lane; k < k1; k += 32) s += L.cor_val[k] * dens[(int64_t)d * L.nsrc_el + L.cor_col[k]];
+    // BtV double layer: - (N - Q) of dG/dn_y times g
+    if (dens_dl)
+      for (int64_t k = k0 + lane; k < k1; k += 32) s -= L.cor_val_dl[k] * dens_dl[(int64_t)d * L.nsrc_el + L.cor_col[k]];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) out[(int64_t)d * L.ntgt_el + e] = s;
@@ -778,12 +782,181 @@ __global__ void k_elem_sum(DevGeom G, DevTaskLists L, const double* __restrict__
 }
 
 cudaError_t launch_elem_sum(const DevGeom& G, const DevTaskLists& L, const double* phi, int64_t ntgt_pts,
-                            const double* dens_src, int ndens, double* out, cudaStream_t st) {
+                            const double* dens_src, int ndens, double* out, cudaStream_t st, const double* dens_dl) {
   if (L.ntgt_el == 0) return cudaSuccess;
+  if (dens_dl && !L.cor_val_dl) return cudaErrorInvalidValue;
   const int64_t threads = L.ntgt_el * 32;
-  k_elem_sum<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(G, L, phi, ntgt_pts, dens_src, ndens, out);
+  k_elem_sum<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(G, L, phi, ntgt_pts, dens_src, ndens, dens_dl, out);
   return cudaGetLastError();
 }
+
+// ------------------------------------------------- double layer (BtV)
+// Moments of the double-layer density g (Algorithm 3: m^b includes
+// - <gamma_1 (y - c)^b, g>; this pass adds that term).  Box-scaled, with
+// u = (y - c)/s: n . grad_y (u^b) = (1/s) sum_i n_i b_i u^(b - e_i), so
+// mhat^b -= (Wg_j / s) sum_i n_i b_i u_j^(b - e_i), Wg_j = w_j g(elem j),
+// n the unit normal of point j's triangle.
+template <typename T>
+__global__ void k_p2m_dl(DevGeom G, const int* __restrict__ leaves, const T* __restrict__ W, int64_t nsp, int ndp,
+                         T* __restrict__ mom) {
+  extern __shared__ unsigned char smraw[];
+  const int P = G.p, np = G.np;
+  T* pw = reinterpret_cast<T*>(smraw);               // [3][P+1][64]
+  T* wn = pw + 3 * (P + 1) * 64;                     // [ndp][3][64]: Wg n_i / s
+  const int leaf = leaves[blockIdx.x];
+  const double4_32a cs = G.box_cs[leaf];
+  const int2 r = G.box_rng[1][leaf];
+  const double inv_s = 1.0 / cs.w;
+  for (int j0 = r.x; j0 < r.y; j0 += 64) {
+    const int m = min(64, r.y - j0);
+    __syncthreads();
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+      const double4_32a y = G.pt64[1][j0 + j];
+      const T d[3] = {(T)((y.x - cs.x) * inv_s), (T)((y.y - cs.y) * inv_s), (T)((y.z - cs.z) * inv_s)};
+      for (int ax = 0; ax < 3; ++ax) {
+        T v = (T)1;
+        for (int k = 0; k <= P; ++k) { pw[(ax * (P + 1) + k) * 64 + j] = v; v *= d[ax]; }
+      }
+      const double4_32a nr = G.tri_nrm[G.pt_elem[1][j0 + j]];
+      for (int dd = 0; dd < ndp; ++dd) {
+        const double wg = (double)W[(int64_t)dd * nsp + j0 + j] * inv_s;
+        wn[(dd * 3 + 0) * 64 + j] = (T)(wg * nr.x);
+        wn[(dd * 3 + 1) * 64 + j] = (T)(wg * nr.y);
+        wn[(dd * 3 + 2) * 64 + j] = (T)(wg * nr.z);
+      }
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < np; q += blockDim.x) {
+      const int mi = G.mi[q];
+      const int a = mi & 255, b = (mi >> 8) & 255, c = (mi >> 16) & 255;
+      const T* px = pw + (0 * (P + 1)) * 64;
+      const T* py = pw + (1 * (P + 1)) * 64;
+      const T* pz = pw + (2 * (P + 1)) * 64;
+      for (int dd = 0; dd < ndp; ++dd) {
+        const T* wx = wn + (dd * 3 + 0) * 64;
+        const T* wy = wn + (dd * 3 + 1) * 64;
+        const T* wz = wn + (dd * 3 + 2) * 64;
+        T acc = 0;
+        for (int j = 0; j < m; ++j) {
+          T g = 0;
+          if (a) g += (T)a * wx[j] * px[(a - 1) * 64 + j] * py[b * 64 + j] * pz[c * 64 + j];
+          if (b) g += (T)b * wy[j] * px[a * 64 + j] * py[(b - 1) * 64 + j] * pz[c * 64 + j];
+          if (c) g += (T)c * wz[j] * px[a * 64 + j] * py[b * 64 + j] * pz[(c - 1) * 64 + j];
+          acc += g;
+        }
+        mom[((int64_t)leaf * ndp + dd) * G.ms + q] -= acc;
+      }
+    }
+  }
+}
+
+template <typename T>
+cudaError_t launch_p2m_dl(const DevGeom& G, const DevTaskLists& L, const T* W, int64_t nsrc_pts, int ndp, T* mom,
+                          cudaStream_t st) {
+  if (L.n_p2m == 0) return cudaSuccess;
+  const size_t sm = sizeof(T) * (3 * (G.p + 1) * 64 + 3 * ndp * 64);
+  k_p2m_dl<T><<<L.n_p2m, 128, sm, st>>>(G, L.p2m_leaf, W, nsrc_pts, ndp, mom);
+  return cudaGetLastError();
+}
+
+// Near field of the double layer over the extended neighbour list:
+// phi(x) -= (1/4pi) sum_j Wg_j n_j.(x - y_j) / |x - y_j|^3 for the leaf's
+// target points, one CTA per target leaf, one target point per thread
+// (chunks of 128 target points); sources stream through shared memory.
+// FP32: leaf-frame double-float coordinates as in the single-layer pass,
+// tile sums folded into FP64; FP64: plain.
+template <typename T>
+__global__ void __launch_bounds__(128) k_p2p_dl(DevGeom G, DevTaskLists L, const T* __restrict__ W, int64_t nsp,
+                                                int64_t ntp, int ndp, double* __restrict__ phi) {
+  constexpr int kT = 128;
+  __shared__ T sx[kT], sy[kT], sz[kT], snx[kT], sny[kT], snz[kT];
+  __shared__ int pre[kRunBatch + 1], rst[kRunBatch];
+  const int b = blockIdx.x;
+  const int leaf = L.p2p_leaf[b];
+  const int tc = L.tgt_cls;
+  const double4_32a cs = G.box_cs[leaf];
+  float chx, clx, chy, cly, chz, clz;
+  split_df(cs.x, chx, clx); split_df(cs.y, chy, cly); split_df(cs.z, chz, clz);
+  const int2 tr = G.box_rng[tc][leaf];
+  const int nt = tr.y - tr.x;
+  const int r0 = L.run_off[b], r1 = L.run_off[b + 1];
+  for (int t0 = 0; t0 < nt; t0 += kT) {
+  const int t = t0 + threadIdx.x;
+  const bool act = t < nt;
+  T xt = 0, yt = 0, zt = 0;
+  if (act) {
+    if (sizeof(T) == 4) {
+      const float4 h = G.pthi[tc][tr.x + t], l = G.ptlo[tc][tr.x + t];
+      xt = (T)((h.x - chx) + (l.x - clx));
+      yt = (T)((h.y - chy) + (l.y - cly));
+      zt = (T)((h.z - chz) + (l.z - clz));
+    } else {
+      const double4_32a x = G.pt64[tc][tr.x + t];
+      xt = (T)(x.x - cs.x); yt = (T)(x.y - cs.y); zt = (T)(x.z - cs.z);
+    }
+  }
+  for (int d = 0; d < ndp; ++d) {
+    double total = 0.0;
+    for (int rb = r0; rb < r1; rb += kRunBatch) {
+      const int nr = min(kRunBatch, r1 - rb);
+      __syncthreads();
+      scan_runs(L.runs + rb, nr, pre, rst);
+      __syncthreads();
+      const int cnt = pre[nr];
+      for (int v0 = 0; v0 < cnt; v0 += kT) {
+        const int m = min(kT, cnt - v0);
+        __syncthreads();
+        if (threadIdx.x < m) {
+          const int v = v0 + threadIdx.x;
+          const int rr = find_run(pre, nr, v);
+          const int src = rst[rr] + (v - pre[rr]);
+          T px, py, pz;
+          if (sizeof(T) == 4) {
+            const float4 h = G.pthi[1][src], l = G.ptlo[1][src];
+            px = (T)((h.x - chx) + (l.x - clx));
+            py = (T)((h.y - chy) + (l.y - cly));
+            pz = (T)((h.z - chz) + (l.z - clz));
+          } else {
+            const double4_32a y = G.pt64[1][src];
+            px = (T)(y.x - cs.x); py = (T)(y.y - cs.y); pz = (T)(y.z - cs.z);
+          }
+          const double4_32a nr3 = G.tri_nrm[G.pt_elem[1][src]];
+          const T wg = W[(int64_t)d * nsp + src];
+          sx[threadIdx.x] = px; sy[threadIdx.x] = py; sz[threadIdx.x] = pz;
+          snx[threadIdx.x] = wg * (T)nr3.x; sny[threadIdx.x] = wg * (T)nr3.y; snz[threadIdx.x] = wg * (T)nr3.z;
+        }
+        __syncthreads();
+        if (act) {
+          T acc = 0;
+          for (int j = 0; j < m; ++j) {
+            const T dx = xt - sx[j], dy = yt - sy[j], dz = zt - sz[j];
+            const T r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 > (T)0) {
+              const T ri = (sizeof(T) == 4) ? (T)rsqrtf((float)r2) : (T)(1.0 / sqrt((double)r2));
+              acc += (snx[j] * dx + sny[j] * dy + snz[j] * dz) * ri * ri * ri;
+            }
+          }
+          total += (double)acc;
+        }
+      }
+    }
+    if (act) phi[(int64_t)d * ntp + tr.x + t] -= total * kInv4Pi;
+  }
+  }
+}
+
+template <typename T>
+cudaError_t launch_p2p_dl(const DevGeom& G, const DevTaskLists& L, const T* W, int64_t nsrc_pts, int64_t ntgt_pts,
+                          int ndp, double* phi, cudaStream_t st) {
+  if (L.n_p2p == 0) return cudaSuccess;
+  k_p2p_dl<T><<<L.n_p2p, 128, 0, st>>>(G, L, W, nsrc_pts, ntgt_pts, ndp, phi);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_p2m_dl<float>(const DevGeom&, const DevTaskLists&, const float*, int64_t, int, float*, cudaStream_t);
+template cudaError_t launch_p2m_dl<double>(const DevGeom&, const DevTaskLists&, const double*, int64_t, int, double*, cudaStream_t);
+template cudaError_t launch_p2p_dl<float>(const DevGeom&, const DevTaskLists&, const float*, int64_t, int64_t, int, double*, cudaStream_t);
+template cudaError_t launch_p2p_dl<double>(const DevGeom&, const DevTaskLists&, const double*, int64_t, int64_t, int, double*, cudaStream_t);
 
 template cudaError_t launch_weights<float>(const DevGeom&, int, int64_t, const double*, int64_t, int, int, float*, cudaStream_t);
 template cudaError_t launch_weights<double>(const DevGeom&, int, int64_t, const double*, int64_t, int, int, double*, cudaStream_t);

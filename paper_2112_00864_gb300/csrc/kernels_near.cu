@@ -56,6 +56,20 @@ __device__ double tri_pot(V3 x, const V3* P) {
   return acc - fabs(w) * fabs(omega);
 }
 
+// int_T n.(x-y)/|x-y|^3 ds_y over the flat triangle with normal
+// n = (P1-P0) x (P2-P0) / |.|: the solid angle T subtends at x, signed
+// positive on the side n points to (for y in the plane n.(x-y) is the
+// height of x).  Van Oosterom-Strackee: tan(Omega/2) = r1.(r2 x r3) /
+// (l1 l2 l3 + (r1.r2) l3 + (r1.r3) l2 + (r2.r3) l1), r_i = P_i - x; the
+// triple product is negative for x on the + side, hence the minus sign.
+__device__ double tri_solid(V3 x, const V3* P) {
+  const V3 r1 = vsub(P[0], x), r2 = vsub(P[1], x), r3 = vsub(P[2], x);
+  const double l1 = sqrt(vdot(r1, r1)), l2 = sqrt(vdot(r2, r2)), l3 = sqrt(vdot(r3, r3));
+  const double num = vdot(r1, vcross(r2, r3));
+  const double den = l1 * l2 * l3 + vdot(r1, r2) * l3 + vdot(r1, r3) * l2 + vdot(r2, r3) * l1;
+  return -2.0 * atan2(num, den);
+}
+
 // int_tet dy/|x-y| = 1/2 sum_F h_F(x) I_F(x), h_F = n_F.(y_F - x), n_F
 // outward, with I_F the flat-triangle integral above.  Everything that does
 // not depend on x (face normals, edge directions, in-plane edge normals) is
@@ -164,7 +178,8 @@ __global__ void k_near_rule(int task, int64_t nnz, const int64_t* __restrict__ s
   if (ii >= nnz) return;
   const int64_t kk = sel ? sel[ii] : ii;
   const int t = row[kk], s = col[kk];
-  const bool tgt_tet = (task != 1), src_tet = (task != 2);
+  // task 3: BtV double layer, kernel dG/dn_y of the source triangle
+  const bool tgt_tet = (task != 1), src_tet = (task != 2 && task != 3), dl = (task == 3);
   const int nvt = tgt_tet ? 4 : 3, nvs = src_tet ? 4 : 3;
   V3 tv[4], sv[4] = {};
   for (int i = 0; i < nvt; ++i) tv[i] = {tgt_v[(int64_t)t * 3 * nvt + 3 * i], tgt_v[(int64_t)t * 3 * nvt + 3 * i + 1], tgt_v[(int64_t)t * 3 * nvt + 3 * i + 2]};
@@ -220,9 +235,14 @@ __global__ void k_near_rule(int task, int64_t nnz, const int64_t* __restrict__ s
       x.z = v[0].z + x1 * (v[1].z - v[0].z) + x2 * (v[2].z - v[0].z);
       wt = gw[ia] * gw[ib] * jac * tri_area2(v);
     }
-    sum += wt * (src_tet ? tet_pot(x, S) : tri_pot(x, sv));
+    sum += wt * (src_tet ? tet_pot(x, S) : dl ? tri_solid(x, sv) : tri_pot(x, sv));
   }
   sum *= kInv4PiN;
+  V3 ns = {0, 0, 0};
+  if (dl) {
+    ns = vcross(vsub(sv[1], sv[0]), vsub(sv[2], sv[0]));
+    ns = vscale(ns, 1.0 / sqrt(vdot(ns, ns)));
+  }
   // product rule of the point passes for this pair
   const int nqt = tgt_tet ? 4 : 3, nqs = src_tet ? 4 : 3;
   double q = 0.0;
@@ -232,7 +252,10 @@ __global__ void k_near_rule(int task, int64_t nnz, const int64_t* __restrict__ s
     const double* yp = src_qp + 3 * ((int64_t)s * nqs + j);
     const double dx = xp[0] - yp[0], dy = xp[1] - yp[1], dz = xp[2] - yp[2];
     const double r = sqrt(dx * dx + dy * dy + dz * dz);
-    if (r != 0.0) q = tgt_qw[(int64_t)t * nqt + i] * src_qw[(int64_t)s * nqs + j] * kInv4PiN / r;
+    if (r != 0.0) {
+      q = tgt_qw[(int64_t)t * nqt + i] * src_qw[(int64_t)s * nqs + j] * kInv4PiN / r;
+      if (dl) q *= (ns.x * dx + ns.y * dy + ns.z * dz) / (r * r);
+    }
   }
   double c = sum - q;
 #pragma unroll

@@ -1,0 +1,146 @@
+"""BtV with the double layer (Algorithm 3: moments <gamma_1 (y-c)^b, g>,
+near field dG/dn_y, FP64 double-layer corrections) and Sec. 5's Green
+representation tests on the GPU.
+
+The library's BtV with densities q (single layer) and g (double layer)
+against the oracle's btv(q) - btv_dl(g): the FP64 path against O2 on the
+same tree (arithmetic only), the FP32 form against O2 and O1; then the
+Green representation of u_L (harmonic) and of u_P (Poisson, with VtV) on
+ball meshes up to level 4, where the error against the analytic cell
+averages falls at least at the paper's O(h).  Norms over cell averages.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2112_00864_gb300.inputs import ball_bc_mesh, cube_bc_mesh, densities
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2112_00864_gb300 import bcfmm
+    from paper_2112_00864_gb300.build import build
+    build()
+    return bcfmm
+
+
+def rel(a, b, size):
+    a, b = np.asarray(a) / size, np.asarray(b) / size
+    return np.linalg.norm(a - b) / np.linalg.norm(b), np.abs(a - b).max() / np.abs(b).max()
+
+
+@pytest.fixture(scope="module")
+def c1():
+    m = cube_bc_mesh(0.25, 0.125)
+    f, q = densities(m, "sine")
+    g = np.cos(2.0 * m.tri_centroids()[:, 0])[None] + 0.5
+    return m, q, g
+
+
+def _btv(bc, m, q, g, **kw):
+    ctx = bc.Context.from_mesh(m, double_layer=1, **kw)
+    ctx.set_density(bc.BOUNDARY, q)
+    ctx.set_density(bc.DIPOLE, g)
+    u = ctx.eval_btv().cpu().numpy()
+    assert ctx.stats()["device_error"] == 0
+    return ctx, u
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 5e-7)])
+def test_double_layer_matches_oracle_fmm(bc, c1, prec, tol):
+    """Same tree, same p: the library's V~q - K~g against O2's."""
+    m, q, g = c1
+    _, u = _btv(bc, m, q, g, p=5, leaf_size=32, precision=prec)
+    ref = O.fmm("btv", m, q, p=5, leaf_size=32) - O.fmm("btv_dl", m, g, p=5, leaf_size=32)
+    r2, rm = rel(u, ref, O.element_volumes(m))
+    assert r2 <= tol, (prec, r2, rm)
+
+
+def test_double_layer_against_direct_definition(bc, c1):
+    """The FP32 form at the paper's order schedule against O1 (the discrete
+    operator summed pair by pair) on sampled targets, and removing g gives
+    the single layer alone."""
+    m, q, g = c1
+    ctx, u = _btv(bc, m, q, g, p=8, q0=6, leaf_size=32, precision="fp32")
+    idx = np.sort(np.random.default_rng(4).choice(m.ntet, 400, replace=False))
+    ref = O.direct("btv", m, q, targets=idx)[0] - O.direct("btv_dl", m, g, targets=idx)[0]
+    r2, rm = rel(u[0][idx], ref, O.element_volumes(m)[idx])
+    assert r2 <= 1e-6, (r2, rm)
+    ctx.clear_dipole()
+    u1 = ctx.eval_btv().cpu().numpy()[0][idx]
+    r2, _ = rel(u1, O.direct("btv", m, q, targets=idx)[0], O.element_volumes(m)[idx])
+    assert r2 <= 1e-6, r2
+
+
+def test_double_layer_of_unit_density(bc):
+    """K~[1] = -1 inside (Green representation of u = 1): g = 1 with q = 0
+    gives cell averages -1 up to the product rule of the far pairs."""
+    m = ball_bc_mesh(2, radial=0.35)
+    _, u = _btv(bc, m, np.zeros((1, m.ntri)), np.ones((1, m.ntri)), p=6, leaf_size=64, precision="fp32")
+    avg = u[0] / O.element_volumes(m)
+    assert np.abs(avg - 1.0).max() < 3e-3, np.abs(avg - 1.0).max()
+
+
+_B4 = np.array([[(5 + 3 * 5 ** 0.5) / 20] + [(5 - 5 ** 0.5) / 20] * 3,
+                [(5 - 5 ** 0.5) / 20, (5 + 3 * 5 ** 0.5) / 20] + [(5 - 5 ** 0.5) / 20] * 2,
+                [(5 - 5 ** 0.5) / 20] * 2 + [(5 + 3 * 5 ** 0.5) / 20, (5 - 5 ** 0.5) / 20],
+                [(5 - 5 ** 0.5) / 20] * 3 + [(5 + 3 * 5 ** 0.5) / 20]])
+_B3 = np.array([[2 / 3, 1 / 6, 1 / 6], [1 / 6, 2 / 3, 1 / 6], [1 / 6, 1 / 6, 2 / 3]])
+
+
+def _p0_data(m, u, du):
+    tri = m.verts[m.tris]
+    n = np.cross(tri[:, 1] - tri[:, 0], tri[:, 2] - tri[:, 0])
+    n /= np.linalg.norm(n, axis=1)[:, None]
+    qp = np.einsum("qk,tkd->tqd", _B3, tri)
+    return u(qp).mean(1), du(qp, n[:, None, :]).mean(1)
+
+
+def _cell_avg(m, u):
+    return u(np.einsum("qk,tkd->tqd", _B4, m.verts[m.tets])).mean(1)
+
+
+def test_green_representation_laplace_gpu(bc):
+    """Sec. 5's BtV test on ball meshes of levels 2..4 (up to 1.9e5 tets):
+    V~[gamma_1 u_L] - K~[gamma_0 u_L] = u_L, u_L = 1/|x - (3,0,0)|; the
+    relative L2 error of the cell averages falls by >= 1.8x per level."""
+    x0 = np.array([3.0, 0.0, 0.0])
+    uL = lambda x: 1.0 / np.linalg.norm(x - x0, axis=-1)
+    duL = lambda x, n: -np.sum((x - x0) * n, -1) / np.linalg.norm(x - x0, axis=-1) ** 3
+    err = []
+    for lev in (2, 3, 4):
+        m = ball_bc_mesh(lev, radial=0.35)
+        g, q = _p0_data(m, uL, duL)
+        _, u = _btv(bc, m, q[None], g[None], p=7, q0=4, leaf_size=128, precision="fp32")
+        ref = _cell_avg(m, uL)
+        num = u[0] / O.element_volumes(m)
+        err.append(np.linalg.norm(num - ref) / np.linalg.norm(ref))
+    assert err[0] > 1.8 * err[1] > 1.8 ** 2 * err[2], err
+
+
+def test_green_representation_poisson_gpu(bc):
+    """Sec. 5's VtV test: V~[gamma_1 u_P] - K~[gamma_0 u_P] + N~f = u_P,
+    u_P = exp(-r^2), f = (6 - 4 r^2) exp(-r^2), VtV and BtV from one
+    context; O(h) or better over ball levels 2..4."""
+    uP = lambda x: np.exp(-np.sum(x * x, -1))
+    fP = lambda x: (6 - 4 * np.sum(x * x, -1)) * np.exp(-np.sum(x * x, -1))
+    duP = lambda x, n: -2 * np.sum(x * n, -1) * uP(x)
+    err = []
+    for lev in (2, 3, 4):
+        m = ball_bc_mesh(lev, radial=0.35)
+        g, q = _p0_data(m, uP, duP)
+        ctx = bc.Context.from_mesh(m, double_layer=1, p=7, q0=4, leaf_size=128, precision="fp32")
+        ctx.set_density(bc.VOLUME, _cell_avg(m, fP)[None])
+        ctx.set_density(bc.BOUNDARY, q[None])
+        ctx.set_density(bc.DIPOLE, g[None])
+        u = (ctx.eval_vtv() + ctx.eval_btv()).cpu().numpy()[0]
+        assert ctx.stats()["device_error"] == 0
+        num = u / O.element_volumes(m)
+        ref = _cell_avg(m, uP)
+        err.append(np.linalg.norm(num - ref) / np.linalg.norm(ref))
+    assert err[0] > 1.8 * err[1] > 1.8 ** 2 * err[2], err

@@ -329,3 +329,129 @@ def test_cube_total_and_ball_closed_form():
     # single layer of g = 1 on the sphere equals 1 inside (to O(h^2))
     ui = O.direct("btv", b, np.ones(b.ntri), targets=tgt)[0] / vol[tgt]
     assert np.abs(ui - 1).max() < 0.03
+
+
+# --- double layer (Algorithm 3, K~[gamma_0 u]) and the Green representation (Sec. 5)
+def test_solid_angle_closed_form():
+    """int_T n.(x-y)/|x-y|^3 ds_y (the double-layer potential of a flat
+    triangle with unit density) is the signed solid angle: over a closed
+    outward-oriented polyhedral surface it adds up to -4 pi inside and 0
+    outside (Gauss), far away it tends to |T| n.(x-c)/|x-c|^3, and it is
+    positive on the side the right-hand-rule normal points to; against
+    brute-force quadrature on a near point."""
+    m = ball_bc_mesh(1, radial=0.35)
+    tri = m.verts[m.tris]
+    for x in ([0.1, -0.2, 0.05], [0.0, 0.0, 0.0], [0.5, 0.4, -0.3]):
+        s = sum(O.tri_solid_angle(np.array(x), t) for t in tri)
+        assert abs(s / (4 * np.pi) + 1.0) < 1e-12, (x, s)
+    for x in ([1.7, 0.3, -0.2], [0.0, -3.0, 0.1]):
+        assert abs(sum(O.tri_solid_angle(np.array(x), t) for t in tri)) < 1e-12
+    t = np.array([[0.0, 0, 0], [1, 0, 0], [0, 1, 0]])
+    c = t.mean(0)
+    for x in ([0.3, 0.2, 50.0], [-20.0, 5.0, -30.0]):
+        x = np.array(x)
+        ref = 0.5 * (x - c)[2] / np.linalg.norm(x - c) ** 3
+        assert abs(O.tri_solid_angle(x, t) - ref) < 1e-3 * abs(ref)
+    assert O.tri_solid_angle(np.array([0.2, 0.2, 0.1]), t) > 0 > O.tri_solid_angle(np.array([0.2, 0.2, -0.1]), t)
+    # brute force: tensor Gauss rule on the collapsed square
+    x = np.array([0.25, 0.3, 0.4])
+    gx, gw = np.polynomial.legendre.leggauss(80)
+    gx, gw = 0.5 * (gx + 1), 0.5 * gw
+    U, Vv = np.meshgrid(gx, gx, indexing="ij")
+    W = np.outer(gw, gw) * (1 - U)
+    y = np.stack([U, (1 - U) * Vv, 0 * U], -1)
+    d = x - y
+    bf = np.sum(W * d[..., 2] / np.linalg.norm(d, axis=-1) ** 3)
+    assert abs(O.tri_solid_angle(x, t) - bf) < 1e-9 * abs(bf)
+
+
+def test_double_layer_of_constant_density():
+    """K~[1] = -1 inside the domain (the Green representation of u = 1),
+    so the discrete double-layer operator maps g = 1 to -|t| on every target
+    tet: exactly when every pair takes the near rule (closed-form solid
+    angle, any outer rule integrates the constant sum exactly), and to
+    product-rule accuracy with the default near/far split."""
+    m = ball_bc_mesh(1, radial=0.35)
+    tg = np.arange(0, m.ntet, 7)
+    vol = O.element_volumes(m)[tg]
+    u = O.direct("btv_dl", m, np.ones((1, m.ntri)), targets=tg, eta_ns=0.0)[0] / vol
+    assert np.abs(u + 1.0).max() < 1e-12
+    u = O.direct("btv_dl", m, np.ones((1, m.ntri)), targets=tg)[0] / vol
+    assert np.abs(u + 1.0).max() < 3e-3
+
+
+def test_fmm_double_layer_converges_to_direct_geometrically():
+    """O2's double-layer leg (moments <gamma_1 (y-c)^beta, g>, near field
+    with dG/dn_y, Algorithm 3) against O1: geometric decay in p."""
+    m = cube_bc_mesh(0.25, 0.25)
+    f, g = densities(m, "sine")
+    u1 = O.direct("btv_dl", m, g)
+    e = []
+    for p in (2, 4, 6, 8):
+        u2 = O.fmm("btv_dl", m, g, p=p, leaf_size=16)
+        e.append(np.linalg.norm(u2 - u1) / np.linalg.norm(u1))
+    assert e[0] > 4 * e[1] > 16 * e[2] > 64 * e[3], e
+    assert e[3] < 2e-6, e
+
+
+_B4 = np.array([[(5 + 3 * 5 ** 0.5) / 20] + [(5 - 5 ** 0.5) / 20] * 3,
+                [(5 - 5 ** 0.5) / 20, (5 + 3 * 5 ** 0.5) / 20] + [(5 - 5 ** 0.5) / 20] * 2,
+                [(5 - 5 ** 0.5) / 20] * 2 + [(5 + 3 * 5 ** 0.5) / 20, (5 - 5 ** 0.5) / 20],
+                [(5 - 5 ** 0.5) / 20] * 3 + [(5 + 3 * 5 ** 0.5) / 20]])
+_B3 = np.array([[2 / 3, 1 / 6, 1 / 6], [1 / 6, 2 / 3, 1 / 6], [1 / 6, 1 / 6, 2 / 3]])
+
+
+def _p0_boundary_data(m, u, du):
+    """P0 Dirichlet and Neumann data: triangle averages of u and du/dn (3-point rule)."""
+    tri = m.verts[m.tris]
+    n = np.cross(tri[:, 1] - tri[:, 0], tri[:, 2] - tri[:, 0])
+    n /= np.linalg.norm(n, axis=1)[:, None]
+    qp = np.einsum("qk,tkd->tqd", _B3, tri)
+    return u(qp).mean(1), du(qp, n[:, None, :]).mean(1)
+
+
+def _cell_avg(m, u, tg):
+    return u(np.einsum("qk,tkd->tqd", _B4, m.verts[m.tets[tg]])).mean(1)
+
+
+def test_green_representation_laplace():
+    """Sec. 5's BtV test: u_L = 1/|x - (3,0,0)| is harmonic in the ball, so
+    V~[gamma_1 u_L] - K~[gamma_0 u_L] = u_L inside (Eq. green:ie:vol with
+    f = 0).  With P0 boundary data the cell averages converge at least at
+    the paper's O(h): the error falls by >= 1.8x per halving of h."""
+    x0 = np.array([3.0, 0.0, 0.0])
+    uL = lambda x: 1.0 / np.linalg.norm(x - x0, axis=-1)
+    duL = lambda x, n: -np.sum((x - x0) * n, -1) / np.linalg.norm(x - x0, axis=-1) ** 3
+    err = []
+    for lev in (1, 2, 3):
+        m = ball_bc_mesh(lev, radial=0.35)
+        g, q = _p0_boundary_data(m, uL, duL)
+        tg = np.sort(np.random.default_rng(0).choice(m.ntet, min(300, m.ntet), replace=False))
+        vol = O.element_volumes(m)[tg]
+        num = (O.direct("btv", m, q[None], targets=tg)[0] - O.direct("btv_dl", m, g[None], targets=tg)[0]) / vol
+        ref = _cell_avg(m, uL, tg)
+        err.append(np.linalg.norm(num - ref) / np.linalg.norm(ref))
+    assert err[0] > 1.8 * err[1] > 1.8 ** 2 * err[2], err
+    assert err[2] < 1e-3, err
+
+
+def test_green_representation_poisson():
+    """Sec. 5's VtV test: u_P = exp(-r^2) solves -Lap u_P = f = (6 - 4 r^2)
+    exp(-r^2), so V~[gamma_1 u_P] - K~[gamma_0 u_P] + N~f = u_P inside
+    (Eq. green:ie:vol), on the ball and on the cube; O(h) or better."""
+    uP = lambda x: np.exp(-np.sum(x * x, -1))
+    fP = lambda x: (6 - 4 * np.sum(x * x, -1)) * np.exp(-np.sum(x * x, -1))
+    duP = lambda x, n: -2 * np.sum(x * n, -1) * uP(x)
+    for mk in (lambda l: ball_bc_mesh(l + 1, radial=0.35), lambda l: cube_bc_mesh(0.5 / 2 ** l, 0.25 / 2 ** l)):
+        err = []
+        for lev in (0, 1, 2):
+            m = mk(lev)
+            g, q = _p0_boundary_data(m, uP, duP)
+            f = _cell_avg(m, fP, np.arange(m.ntet))
+            tg = np.sort(np.random.default_rng(1).choice(m.ntet, min(200, m.ntet), replace=False))
+            vol = O.element_volumes(m)[tg]
+            num = (O.direct("btv", m, q[None], targets=tg)[0] - O.direct("btv_dl", m, g[None], targets=tg)[0]
+                   + O.direct("vtv", m, f[None], targets=tg)[0]) / vol
+            ref = _cell_avg(m, uP, tg)
+            err.append(np.linalg.norm(num - ref) / np.linalg.norm(ref))
+        assert err[0] > 1.8 * err[1] > 1.8 ** 2 * err[2], err
