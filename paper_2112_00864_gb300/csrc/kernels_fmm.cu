@@ -298,6 +298,19 @@ __device__ __forceinline__ void l2p_and_store(const DevGeom& G, int leaf, int nd
   for (int d = 0; d < ND; ++d) phi[(int64_t)d * ntp + pos] = near[d] * kInv4Pi + (double)far[d];
 }
 
+// The hardware reciprocal square root (PTX rsqrt.approx.ftz.f32: maximum
+// relative error about 2^-22.9, subnormal inputs and results flushed to
+// zero).  Squared distances of distinct quadrature points lie far above the
+// subnormal range; r^2 = 0 is selected out where it can occur, and the
+// padding point's r^2 = inf gives 0.  Without the flush the compiler wraps
+// the same instruction in a subnormal rescaling that costs several extra
+// instructions per pair.
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 __device__ __forceinline__ void two_sum_f(float& hi, float& lo, float x) {
   const float s = hi + x;
   const float bb = s - hi;
@@ -407,7 +420,7 @@ __global__ void __launch_bounds__(128) k_p2p_l2p_f32(DevGeom G, DevTaskLists L, 
           for (int u = 0; u < TPT; ++u) {
             const float dx = xt[u] - s.x, dy = yt[u] - s.y, dz = zt[u] - s.z;
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const float ri = r2 > 0.f ? rsqrtf(r2) : 0.f;
+            const float ri = r2 > 0.f ? rsqrt_ftz(r2) : 0.f;
             acc[u][0] = fmaf(s.w, ri, acc[u][0]);
 #pragma unroll
             for (int d = 1; d < ND; ++d) acc[u][d] = fmaf(tw[cur][d - 1][j], ri, acc[u][d]);
@@ -421,7 +434,7 @@ __global__ void __launch_bounds__(128) k_p2p_l2p_f32(DevGeom G, DevTaskLists L, 
           for (int u = 0; u < TPT; ++u) {
             const float dx = xt[u] - s.x, dy = yt[u] - s.y, dz = zt[u] - s.z;
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const float ri = rsqrtf(r2);
+            const float ri = rsqrt_ftz(r2);
             acc[u][0] = fmaf(s.w, ri, acc[u][0]);
 #pragma unroll
             for (int d = 1; d < ND; ++d) acc[u][d] = fmaf(tw[cur][d - 1][j], ri, acc[u][d]);
@@ -586,7 +599,7 @@ __global__ void __launch_bounds__(128) k_p2p_l2p_f32x2(DevGeom G, DevTaskLists L
           for (int u = 0; u < TPT; ++u) {
             const float2 dx = __fadd2_rn(X[u], nx), dy = __fadd2_rn(Y[u], ny), dz = __fadd2_rn(Z[u], nz);
             const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
-            const float2 ri = make_float2(r2.x > 0.f ? rsqrtf(r2.x) : 0.f, r2.y > 0.f ? rsqrtf(r2.y) : 0.f);
+            const float2 ri = make_float2(r2.x > 0.f ? rsqrt_ftz(r2.x) : 0.f, r2.y > 0.f ? rsqrt_ftz(r2.y) : 0.f);
 #pragma unroll
             for (int d = 0; d < ND; ++d)
               acc[u][d] = __ffma2_rn(reinterpret_cast<const float2*>(sw[cur][d])[k], ri, acc[u][d]);
@@ -600,7 +613,7 @@ __global__ void __launch_bounds__(128) k_p2p_l2p_f32x2(DevGeom G, DevTaskLists L
           for (int u = 0; u < TPT; ++u) {
             const float2 dx = __fadd2_rn(X[u], nx), dy = __fadd2_rn(Y[u], ny), dz = __fadd2_rn(Z[u], nz);
             const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
-            const float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+            const float2 ri = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
 #pragma unroll
             for (int d = 0; d < ND; ++d)
               acc[u][d] = __ffma2_rn(reinterpret_cast<const float2*>(sw[cur][d])[k], ri, acc[u][d]);
@@ -932,7 +945,7 @@ __global__ void __launch_bounds__(128) k_p2p_dl(DevGeom G, DevTaskLists L, const
             const T dx = xt - sx[j], dy = yt - sy[j], dz = zt - sz[j];
             const T r2 = dx * dx + dy * dy + dz * dz;
             if (r2 > (T)0) {
-              const T ri = (sizeof(T) == 4) ? (T)rsqrtf((float)r2) : (T)(1.0 / sqrt((double)r2));
+              const T ri = (sizeof(T) == 4) ? (T)rsqrt_ftz((float)r2) : (T)(1.0 / sqrt((double)r2));
               acc += (snx[j] * dx + sny[j] * dy + snz[j] * dz) * ri * ri * ri;
             }
           }
