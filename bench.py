@@ -605,18 +605,23 @@ def run_learned(args):
 
 
 def run_largest(args):
-    """Config 5: unit cube at h = 1/32, 1/64, 1/128 with f = exp(-|x-c|^2/0.05)
-    and g = cos 2 pi x cos 2 pi y cos 2 pi z; VtV + VtB + BtV at p = 8 (FP32 on
-    CUDA cores: the tensor-core M2L stops at p = 7) with the learned
-    near-singular correction for VtV and VtB.  Per h: setup, step time, accuracy on sampled
-    targets against the context's own discrete operator summed pair by pair in FP64 on the
-    GPU (the far-field error; the learned correction's own error is measured by the learned
-    workload); across h: the observed convergence of the energies
-    sum_t f_t u_t (VtV) and sum_t g-driven u_t f_t (BtV)."""
+    """Config 5 and the paper's convergence study (Sec. 5): BC cube meshes of
+    [0,1]^3 at h = 1/32, 1/64, 1/128 (the last 2.5e6 tets), VtV + VtB + BtV
+    (single and double layer) in the chosen FP32 form, orders capped at p = 8
+    (q_l = min(8, q0 + L - l)), the learned near-singular correction for VtV and
+    VtB.  Data: the paper's test functions in the paper's frame
+    x' = 2 (x - (1/2, 1/2, 1/2)) (its domain [-1,1]^3): u_P = exp(-|x'|^2) with
+    f = -Lap u_P = 4 (6 - 4|x'|^2) exp(-|x'|^2), and u_L = 1/|x' - (3,0,0)|;
+    P0 data = element averages.  Per h: setup, step time, accuracy on sampled
+    targets against the context's own discrete operator summed pair by pair in
+    FP64 on the GPU; the per-element error of the Green representations
+    V~[gamma_1 u] - K~[gamma_0 u] (+ N~f) against the analytic cell averages
+    of u_L (BtV) and u_P (VtV + BtV) over every tet; across h: the observed
+    orders log2(e_h / e_h/2)."""
     import torch
     from paper_2112_00864_gb300 import bcfmm, learned
     from paper_2112_00864_gb300.build import build
-    from paper_2112_00864_gb300.inputs import cube_bc_mesh, densities
+    from paper_2112_00864_gb300.inputs import cube_bc_mesh
     build()
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
@@ -627,54 +632,92 @@ def run_largest(args):
     blob, rep = learned.train_blob(tasks=("vtv", "vtb"))
     train_s = time.perf_counter() - t0
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    prm = dict(p=8, eta0=0.5, leaf_size=128, precision="fp32", near_mode="learned", mlp_blob=blob)
-    levels, energies = [], []
+    prm = dict(CHOSEN, p=8, near_mode="learned", mlp_blob=blob, double_layer=1)
+    c = np.array([0.5, 0.5, 0.5])
+    xp = lambda x: 2.0 * (x - c)
+    uP = lambda x: np.exp(-np.sum(xp(x) ** 2, -1))
+    fP = lambda x: 4.0 * (6.0 - 4.0 * np.sum(xp(x) ** 2, -1)) * np.exp(-np.sum(xp(x) ** 2, -1))
+    duP = lambda x, n: -4.0 * np.sum(xp(x) * n, -1) * uP(x)
+    x0 = np.array([3.0, 0.0, 0.0])
+    uL = lambda x: 1.0 / np.linalg.norm(xp(x) - x0, axis=-1)
+    duL = lambda x, n: -2.0 * np.sum((xp(x) - x0) * n, -1) / np.linalg.norm(xp(x) - x0, axis=-1) ** 3
+    b4 = np.array([[(5 + 3 * 5 ** 0.5) / 20] + [(5 - 5 ** 0.5) / 20] * 3,
+                   [(5 - 5 ** 0.5) / 20, (5 + 3 * 5 ** 0.5) / 20] + [(5 - 5 ** 0.5) / 20] * 2,
+                   [(5 - 5 ** 0.5) / 20] * 2 + [(5 + 3 * 5 ** 0.5) / 20, (5 - 5 ** 0.5) / 20],
+                   [(5 - 5 ** 0.5) / 20] * 3 + [(5 + 3 * 5 ** 0.5) / 20]])
+    b3 = np.array([[2 / 3, 1 / 6, 1 / 6], [1 / 6, 2 / 3, 1 / 6], [1 / 6, 1 / 6, 2 / 3]])
+    levels = []
     for inv_h in (32, 64, 128):
         m = cube_bc_mesh(1 / inv_h, 1 / inv_h)
-        f, g = densities(m, "gauss")
+        tq = np.einsum("qk,tkd->tqd", b4, m.verts[m.tets])
+        tri = m.verts[m.tris]
+        nrm = np.cross(tri[:, 1] - tri[:, 0], tri[:, 2] - tri[:, 0])
+        nrm /= np.linalg.norm(nrm, axis=1)[:, None]
+        bq = np.einsum("qk,tkd->tqd", b3, tri)
+        f = fP(tq).mean(1)[None]
+        data = {"P": (duP(bq, nrm[:, None]).mean(1)[None], uP(bq).mean(1)[None], uP(tq).mean(1)),
+                "L": (duL(bq, nrm[:, None]).mean(1)[None], uL(bq).mean(1)[None], uL(tq).mean(1))}
+        vol = _sizes(m.verts, m.tets)
         t0 = time.perf_counter()
         ctx = bcfmm.Context.from_mesh(m, stream=stream, **prm)
         setup = time.perf_counter() - t0
-        fd, gd = torch.tensor(f, device="cuda"), torch.tensor(g, device="cuda")
+        fd = torch.tensor(f, device="cuda")
+        qd, gd = (torch.tensor(a, device="cuda") for a in data["P"][:2])
         ctx.set_density(bcfmm.VOLUME, fd)
-        ctx.set_density(bcfmm.BOUNDARY, gd)
+        ctx.set_density(bcfmm.BOUNDARY, qd)
+        ctx.set_density(bcfmm.DIPOLE, gd)
         tasks = ("vtv", "vtb", "btv")
         outs = ctx.eval_graph(tasks)
         for _ in range(args.warmup):
             ctx.eval_graph(tasks, outs)
-        times = _timed_steps(lambda: (ctx.set_density(bcfmm.VOLUME, fd), ctx.set_density(bcfmm.BOUNDARY, gd),
-                                      ctx.eval_graph(tasks, outs)), args.steps, stream, flush)
+        times = _timed_steps(lambda: (ctx.set_density(bcfmm.VOLUME, fd), ctx.set_density(bcfmm.BOUNDARY, qd),
+                                      ctx.set_density(bcfmm.DIPOLE, gd), ctx.eval_graph(tasks, outs)),
+                             args.steps, stream, flush)
         st = ctx.stats()
         u = {t: outs[t].cpu().numpy()[0] for t in tasks}
+        # Green representations against the analytic cell averages, every tet
+        green = {}
+        num = (u["vtv"] + u["btv"]) / vol
+        green["poisson_vtv_btv"] = float(np.linalg.norm(num - data["P"][2]) / np.linalg.norm(data["P"][2]))
+        ctx.set_density(bcfmm.BOUNDARY, data["L"][0])
+        ctx.set_density(bcfmm.DIPOLE, data["L"][1])
+        numL = ctx.eval_btv().cpu().numpy()[0] / vol
+        green["laplace_btv"] = float(np.linalg.norm(numL - data["L"][2]) / np.linalg.norm(data["L"][2]))
+        # the single layer alone against direct sampling (the double layer's
+        # discrete operator has no sampling counterpart)
+        ctx.clear_dipole()
+        ctx.set_density(bcfmm.BOUNDARY, qd)
+        ub = ctx.eval_btv().cpu().numpy()[0]
         rng = np.random.default_rng(inv_h)
         acc = {}
-        for t, n, el in (("vtv", m.ntet, m.tets), ("vtb", m.ntri, m.tris), ("btv", m.ntet, m.tets)):
+        for t, n, el, uu in (("vtv", m.ntet, m.tets, u["vtv"]), ("vtb", m.ntri, m.tris, u["vtb"]),
+                             ("btv", m.ntet, m.tets, ub)):
             idx = np.sort(rng.choice(n, 32, replace=False))
             size = _sizes(m.verts, el[idx])
             ref = ctx.direct_sample(t, idx)[0] / size
-            acc[t] = float(np.linalg.norm(u[t][idx] / size - ref) / np.linalg.norm(ref))
-        energies.append((float(np.dot(f[0], u["vtv"])), float(np.dot(f[0], u["btv"]))))
+            acc[t] = float(np.linalg.norm(uu[idx] / size - ref) / np.linalg.norm(ref))
         ms = float(np.mean(times))
         npts = 4 * m.ntet + 3 * m.ntri + 4 * m.ntet
         levels.append({"h": f"1/{inv_h}", "ntet": int(m.ntet), "ntri": int(m.ntri), "setup_s": setup,
                        "near_rule_s": st["near_rule_s"], "ms_per_step": ms, "target_pts_per_s": npts / (ms * 1e-3),
-                       "rel_l2_vs_direct_fp64": acc,
+                       "rel_l2_vs_direct_fp64": acc, "green_rel_l2_vs_analytic": green,
+                       "level_order": st["level_order"],
                        "near_learned_fraction": {t: st[t]["near_learned"] / max(1, st[t]["near_pairs"]) for t in tasks}})
         ctx.close()
         del outs
         torch.cuda.empty_cache()
     rates = {}
-    for k, name in ((0, "vtv_energy"), (1, "btv_energy")):
-        e = [x[k] for x in energies]
-        d1, d2 = abs(e[0] - e[1]), abs(e[1] - e[2])
-        rates[name] = {"values": e, "observed_order": float(math.log2(d1 / d2)) if d2 > 0 else None}
+    for k in ("poisson_vtv_btv", "laplace_btv"):
+        e = [lv["green_rel_l2_vs_analytic"][k] for lv in levels]
+        rates[k] = {"errors": e, "observed_orders": [float(math.log2(e[i] / e[i + 1])) for i in range(len(e) - 1)]}
     big = levels[-1]
     return {
         "metric": METRIC, "value": big["target_pts_per_s"], "unit": "target pts/s (VtV + VtB + BtV)", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": big["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 (P2P, expansions, M2L); learned near-singular; f64 rest",
-        "data": "synthetic: analytic BC cube meshes, Gaussian f, cosine g",
-        "config": {"workload": "unit cube BC meshes h = 1/32, 1/64, 1/128; VtV+VtB+BtV; p = 8 FP32, learned near field",
+        "data": "synthetic: analytic BC cube meshes, the paper's u_P, f and u_L",
+        "config": {"workload": "unit cube BC meshes h = 1/32, 1/64, 1/128; VtV+VtB+BtV with the double layer; "
+                               "orders capped at p = 8, learned near field for VtV/VtB",
                    **{k: v for k, v in prm.items() if k != "mlp_blob"}},
         "levels": levels, "convergence": rates, "training_s": train_s,
     }
@@ -717,13 +760,38 @@ def run_reference(args):
     }
 
 
+def run_kernels(args):
+    """The ball workload's chosen form, eval_vtv then eval_vtb per step
+    (warmup + steps, no L2 flush): the command profilers wrap."""
+    import torch
+    from paper_2112_00864_gb300 import bcfmm
+    from paper_2112_00864_gb300.build import build
+    build()
+    m, f = make_inputs()
+    ctx = bcfmm.Context.from_mesh(m, timing=1, **CHOSEN)
+    fd = torch.tensor(f, device="cuda")
+    ov = torch.empty((1, m.ntet), dtype=torch.float64, device="cuda")
+    ob = torch.empty((1, m.ntri), dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup + args.steps):
+        ctx.set_density(bcfmm.VOLUME, fd)
+        ctx.eval_vtv(ov)
+        ctx.eval_vtb(ob)
+    torch.cuda.synchronize()
+    st = ctx.stats()
+    ctx.close()
+    return {"workload": "kernels", "config": dict(workload(), **CHOSEN), "stage_ms": st["stage_ms"],
+            "device_error": st["device_error"]}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["ball", "batch", "learned", "largest"], default="ball")
+    ap.add_argument("--workload", choices=["ball", "batch", "learned", "largest", "kernels"], default="ball",
+                    help="kernels: the ball workload's chosen form only, task by task (VtV, VtB), "
+                         "for profilers; prints the per-stage times, no oracle, no baselines")
     ap.add_argument("--ball-level", type=int, default=4, help="icosphere level of the ball workload (profiling: 3)")
     args = ap.parse_args()
     global BALL_LEVEL
@@ -737,6 +805,8 @@ def main():
         res = run_learned(args)
     elif args.workload == "largest":
         res = run_largest(args)
+    elif args.workload == "kernels":
+        res = run_kernels(args)
     else:
         res = run_ours(args)
     if res is not None:

@@ -100,8 +100,8 @@ struct bcfmm_ctx {
   DevGeom G{};
   TaskDev task[3];
   // translation tables
-  double *T64 = nullptr, *M2M64 = nullptr, *L2L64 = nullptr;
-  float *T32 = nullptr, *M2M32 = nullptr, *L2L32 = nullptr;
+  double* T64 = nullptr;
+  float* T32 = nullptr;
   M2LTensorTables tc{};
   // learned near-singular correction (near_mode 1): per task, FP32 master
   // parameters and per-bin calibrated errors, from the blob
@@ -789,7 +789,7 @@ static int build_impl(const double* verts, const int64_t* vert_off, const int32_
       return cleanup(fail(BCFMM_ERR_OOM, "build: device allocation failed (normals)"));
     G.tri_nrm = dn;
   }
-  // translation tables: M2L transposed per offset code, M2M / L2L per octant
+  // translation tables: M2L transposed per offset code
   {
     const int np = C->np;
     const int ncode = (int)(H.offsets.size() / 3);
@@ -804,23 +804,27 @@ static int build_impl(const double* verts, const int64_t* vert_off, const int32_
           Tt[((size_t)code * np + b) * np + a] = tmp[a * np + b];
         }
     }
-    std::vector<double> Mm0, Lm0;
-    m2m_matrices(prm.p, Mm0);
-    l2l_matrices(prm.p, Lm0);
-    std::vector<double> Mm(Mm0.size()), Lm(Lm0.size());   // transposed per octant
-    for (int q = 0; q < 8; ++q)
-      for (int a = 0; a < np; ++a)
-        for (int b = 0; b < np; ++b) {
-          Mm[((size_t)q * np + b) * np + a] = Mm0[((size_t)q * np + a) * np + b];
-          Lm[((size_t)q * np + b) * np + a] = Lm0[((size_t)q * np + a) * np + b];
+    // M2M and L2L run as three 1-D binomial shifts: their coefficients
+    // C(n, k) (+-1/4)^(n-k), s = 0 for -1/4, s = 1 for +1/4
+    const int P1 = prm.p + 1;
+    std::vector<double> sh(2 * (size_t)P1 * P1, 0.0);
+    for (int sg = 0; sg < 2; ++sg)
+      for (int n = 0; n < P1; ++n)
+        for (int k = 0; k <= n; ++k) {
+          double c = 1.0;
+          for (int i = 1; i <= k; ++i) c = c * (n - k + i) / i;
+          sh[((size_t)sg * P1 + n) * P1 + k] = c * std::pow(sg ? 0.25 : -0.25, n - k);
         }
-    std::vector<float> Tt32(Tt.begin(), Tt.end()), M32(Mm.begin(), Mm.end()), L32(Lm.begin(), Lm.end());
+    std::vector<float> sh32(sh.begin(), sh.end());
+    std::vector<float> Tt32(Tt.begin(), Tt.end());
+    double* dsh;
+    float* dsh32;
     bool ok = m.upload(&C->T64, Tt.data(), Tt.size(), st) == cudaSuccess &&
-              m.upload(&C->M2M64, Mm.data(), Mm.size(), st) == cudaSuccess &&
-              m.upload(&C->L2L64, Lm.data(), Lm.size(), st) == cudaSuccess &&
               m.upload(&C->T32, Tt32.data(), Tt32.size(), st) == cudaSuccess &&
-              m.upload(&C->M2M32, M32.data(), M32.size(), st) == cudaSuccess &&
-              m.upload(&C->L2L32, L32.data(), L32.size(), st) == cudaSuccess;
+              m.upload(&dsh, sh.data(), sh.size(), st) == cudaSuccess &&
+              m.upload(&dsh32, sh32.data(), sh32.size(), st) == cudaSuccess;
+    C->G.shift64 = dsh;
+    C->G.shift32 = dsh32;
     if (!ok) return cleanup(fail(BCFMM_ERR_OOM, "build: device allocation failed (tables)"));
     if (tc_mode) {
       std::vector<int> orders;
@@ -1326,7 +1330,7 @@ static int eval_impl(bcfmm_ctx* C, int t, double* out, int out_is_device, bool s
       if (dl) CU(launch_p2m_dl<double>(G, L, C->W64dl, nsp, ndp, C->mom64, st));
       for (int l = C->nlevels - 1; l >= 0; --l) {
         const int n = D.m2m_off[l + 1] - D.m2m_off[l];
-        CU(launch_m2m<double>(G, D.m2m_parent + D.m2m_off[l], n, C->M2M64, ndp, C->mom64, st));
+        CU(launch_m2m<double>(G, D.m2m_parent + D.m2m_off[l], n, ndp, C->mom64, st));
       }
     }
     if (tm) CU(cudaEventRecord(ev[2], st));
@@ -1334,7 +1338,7 @@ static int eval_impl(bcfmm_ctx* C, int t, double* out, int out_is_device, bool s
     if (tm) CU(cudaEventRecord(ev[3], st));
     for (int l = 3; l < C->nlevels && !skip_far; ++l) {
       const int n = D.l2l_off[l + 1] - D.l2l_off[l];
-      CU(launch_l2l<double>(G, D.l2l_child + D.l2l_off[l], n, C->L2L64, ndp, C->loc64, st));
+      CU(launch_l2l<double>(G, D.l2l_child + D.l2l_off[l], n, ndp, C->loc64, st));
     }
     if (tm) CU(cudaEventRecord(ev[4], st));
     CU(launch_p2p_l2p_f64(G, L, C->W64, nsp, ntp, ndp, C->loc64, C->phi, st));
@@ -1352,7 +1356,7 @@ static int eval_impl(bcfmm_ctx* C, int t, double* out, int out_is_device, bool s
       if (dl) CU(launch_p2m_dl<float>(G, L, C->W32dl, nsp, ndp, C->mom32, st));
       for (int l = C->nlevels - 1; l >= 0; --l) {
         const int n = D.m2m_off[l + 1] - D.m2m_off[l];
-        CU(launch_m2m<float>(G, D.m2m_parent + D.m2m_off[l], n, C->M2M32, ndp, C->mom32, st));
+        CU(launch_m2m<float>(G, D.m2m_parent + D.m2m_off[l], n, ndp, C->mom32, st));
       }
     }
     if (tm) CU(cudaEventRecord(ev[2], st));
@@ -1369,7 +1373,7 @@ static int eval_impl(bcfmm_ctx* C, int t, double* out, int out_is_device, bool s
     if (tm) CU(cudaEventRecord(ev[3], st));
     for (int l = 3; l < C->nlevels && !skip_far; ++l) {
       const int n = D.l2l_off[l + 1] - D.l2l_off[l];
-      CU(launch_l2l<float>(G, D.l2l_child + D.l2l_off[l], n, C->L2L32, ndp, C->loc32, st));
+      CU(launch_l2l<float>(G, D.l2l_child + D.l2l_off[l], n, ndp, C->loc32, st));
     }
     if (tm) CU(cudaEventRecord(ev[4], st));
     CU(launch_p2p_l2p_f32(G, L, C->W32, nsp, ntp, ndp, C->loc32, C->phi, st));
@@ -1505,7 +1509,7 @@ extern "C" int bcfmm_eval_noalloc(bcfmm_ctx* C, int32_t task, const double* dens
   CU(launch_p2m<float>(G, L, C->W32, nsp, ndp, C->mom32, st));
   for (int l = C->nlevels - 1; l >= 0; --l) {
     const int n = D.m2m_off[l + 1] - D.m2m_off[l];
-    CU(launch_m2m<float>(G, D.m2m_parent + D.m2m_off[l], n, C->M2M32, ndp, C->mom32, st));
+    CU(launch_m2m<float>(G, D.m2m_parent + D.m2m_off[l], n, ndp, C->mom32, st));
   }
   if (tcp) {
     CU(launch_m2l_tc(G, L, D.tcs, C->tc, ndp, C->mom32, C->loc32, partial, C->tc_momb, st));
@@ -1518,7 +1522,7 @@ extern "C" int bcfmm_eval_noalloc(bcfmm_ctx* C, int32_t task, const double* dens
   }
   for (int l = 3; l < C->nlevels; ++l) {
     const int n = D.l2l_off[l + 1] - D.l2l_off[l];
-    CU(launch_l2l<float>(G, D.l2l_child + D.l2l_off[l], n, C->L2L32, ndp, C->loc32, st));
+    CU(launch_l2l<float>(G, D.l2l_child + D.l2l_off[l], n, ndp, C->loc32, st));
   }
   CU(launch_p2p_l2p_f32(G, L, C->W32, nsp, ntp, ndp, C->loc32, C->phi, st));
   CU(launch_elem_sum(G, L, C->phi, ntp, dens_dev, 1, out_dev, st));

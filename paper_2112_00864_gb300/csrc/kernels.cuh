@@ -26,6 +26,8 @@ struct DevGeom {
   const float4* ptlo[2];         // float lo parts (x - hi, ...)
   const int* pt_elem[2];         // sorted point -> element
   const double4_32a* tri_nrm;    // unit normal of each triangle (right-hand rule; w unused)
+  const double* shift64;         // [2][p+1][p+1] C(n, k) (-+1/4)^(n-k): M2M / L2L 1-D shifts
+  const float* shift32;
 };
 
 struct DevTaskLists {
@@ -55,13 +57,13 @@ template <typename T>
 cudaError_t launch_p2m(const DevGeom& G, const DevTaskLists& L, const T* W, int64_t nsrc_pts, int ndp,
                        T* mom, cudaStream_t st);
 template <typename T>
-cudaError_t launch_m2m(const DevGeom& G, const int* parents, int n, const T* M2M, int ndp, T* mom, cudaStream_t st);
+cudaError_t launch_m2m(const DevGeom& G, const int* parents, int n, int ndp, T* mom, cudaStream_t st);
 // sel: optional list of indices into L.m2l_tgt (nsel of them); NULL: every target
 template <typename T>
 cudaError_t launch_m2l_simt(const DevGeom& G, const DevTaskLists& L, const T* Tt, int ndp, const T* mom, T* loc,
                             cudaStream_t st, const int* sel = nullptr, int nsel = 0);
 template <typename T>
-cudaError_t launch_l2l(const DevGeom& G, const int* children, int n, const T* L2L, int ndp, T* loc, cudaStream_t st);
+cudaError_t launch_l2l(const DevGeom& G, const int* children, int n, int ndp, T* loc, cudaStream_t st);
 cudaError_t launch_p2p_l2p_f32(const DevGeom& G, const DevTaskLists& L, const float* W, int64_t nsrc_pts,
                                int64_t ntgt_pts, int ndp, const float* loc, double* phi, cudaStream_t st);
 cudaError_t launch_p2p_l2p_f64(const DevGeom& G, const DevTaskLists& L, const double* W, int64_t nsrc_pts,

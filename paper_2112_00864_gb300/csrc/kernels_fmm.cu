@@ -89,36 +89,115 @@ cudaError_t launch_p2m(const DevGeom& G, const DevTaskLists& L, const T* W, int6
 // ---------------------------------------------------------------- M2M
 // m_parent[b] = sum_children sum_g M[octant][b][g] m_child[g]; the table is
 // stored transposed, Mt[octant][g][b], so threads (b) read it coalesced.
+// Shifts between a box and its child in octant o (centre offset sigma s_p/4,
+// sigma_i = +-1 by the octant's bits; child side s_p/2), box-scaled:
+//   M2M  mhat_p[b] = sum_{g <= b} prod_i C(b_i, g_i) (sigma_i/4)^(b_i - g_i) 2^-|g| mhat_c[g]
+//   L2L  lhat_c[a] = 2^-|a| sum_{b >= a} prod_i C(b_i, a_i) (sigma_i/4)^(b_i - a_i) lhat_p[b]
+// Both factor into three 1-D binomial shifts, one per axis (the Taylor
+// shift of (u + d)^n along each coordinate); every intermediate index stays
+// within the total-degree bound (its components lie between those of the
+// input and the output), so the passes are exact on the truncated arrays.
+// One pass costs about n (p+1)/2 products instead of the dense table's
+// n^2 / 2 (n = nterms(p)), and no table is read from memory.
+
+// degree-major position of the multi-index (i, j, k): degree d, then i
+// descending, then j descending
+__device__ __forceinline__ int midx3(int i, int j, int k) {
+  const int d = i + j + k;
+  return d * (d + 1) * (d + 2) / 6 + (j + k) * (j + k + 1) / 2 + k;
+}
+
+// tab[s][n][k] = C(n, k) (+-1/4)^(n - k), s = 0: -1/4, s = 1: +1/4 (the
+// table is built on the host, G.shift64 / G.shift32)
 template <typename T>
-__global__ void k_m2m(DevGeom G, const int* __restrict__ parents, const T* __restrict__ M2M, int ndp,
-                      T* __restrict__ mom) {
+__device__ __forceinline__ const T* shift_src(const DevGeom& G);
+template <>
+__device__ __forceinline__ const float* shift_src<float>(const DevGeom& G) { return G.shift32; }
+template <>
+__device__ __forceinline__ const double* shift_src<double>(const DevGeom& G) { return G.shift64; }
+template <typename T>
+__device__ void shift_table(const DevGeom& G, T* tab) {
+  const T* src = shift_src<T>(G);
+  for (int e = threadIdx.x; e < 2 * (G.p + 1) * (G.p + 1); e += blockDim.x) tab[e] = src[e];
+}
+
+// one M2M pass along axis ax: out[b] = sum_{g_ax <= b_ax} tab[b_ax][g_ax] in[b with b_ax -> g_ax]
+template <typename T>
+__device__ __forceinline__ void m2m_pass(const DevGeom& G, int nq, int ax, const T* tb, const T* in, T* out) {
+  for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+    const int mi = G.mi[q];
+    int c[3] = {mi & 255, (mi >> 8) & 255, (mi >> 16) & 255};
+    const int n = c[ax];
+    const int P1 = G.p + 1;
+    T acc = 0;
+    for (int k = 0; k <= n; ++k) {
+      c[ax] = k;
+      acc += tb[n * P1 + k] * in[midx3(c[0], c[1], c[2])];
+    }
+    out[q] = acc;
+  }
+}
+
+// one L2L pass along axis ax: out[a] = sum_{b_ax >= a_ax, |b| <= qd} tab[b_ax][a_ax] in[a with a_ax -> b_ax]
+template <typename T>
+__device__ __forceinline__ void l2l_pass(const DevGeom& G, int nq, int qd, int ax, const T* tb, const T* in, T* out) {
+  for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+    const int mi = G.mi[q];
+    int c[3] = {mi & 255, (mi >> 8) & 255, (mi >> 16) & 255};
+    const int a = c[ax], rest = c[0] + c[1] + c[2] - a;
+    const int P1 = G.p + 1;
+    T acc = 0;
+    for (int k = a; k + rest <= qd; ++k) {
+      c[ax] = k;
+      acc += tb[k * P1 + a] * in[midx3(c[0], c[1], c[2])];
+    }
+    out[q] = acc;
+  }
+}
+
+// ---------------------------------------------------------------- M2M
+// One CTA per parent box: the children's moments through the three
+// passes, summed in shared memory.
+template <typename T>
+__global__ void k_m2m(DevGeom G, const int* __restrict__ parents, int ndp, T* __restrict__ mom) {
   extern __shared__ unsigned char smraw[];
-  T* mc = reinterpret_cast<T*>(smraw);               // [8][np]
-  const int np = G.np;
+  const int np = G.np, P1 = G.p + 1;
+  T* tab = reinterpret_cast<T*>(smraw);              // [2][P+1][P+1]
+  T* va = tab + 2 * P1 * P1;                         // [np]
+  T* vb = va + np;                                   // [np]
+  T* acc = vb + np;                                  // [np]
+  shift_table(G, tab);
   const int P = parents[blockIdx.x];
   const int c0 = G.box_child0[P], nc = G.box_nchild[P];
   for (int d = 0; d < ndp; ++d) {
-    __syncthreads();
-    for (int i = threadIdx.x; i < nc * np; i += blockDim.x) {
-      int c = i / np, q = i % np;
-      mc[i] = mom[((int64_t)(c0 + c) * ndp + d) * G.ms + q];
-    }
-    __syncthreads();
-    for (int b = threadIdx.x; b < np; b += blockDim.x) {
-      T acc = 0;
-      for (int c = 0; c < nc; ++c) {
-        const T* Mt = M2M + (int64_t)G.box_octant[c0 + c] * np * np;
-        for (int g = 0; g <= b; ++g) acc += Mt[(int64_t)g * np + b] * mc[c * np + g];   // g <= b
+    for (int q = threadIdx.x; q < np; q += blockDim.x) acc[q] = 0;
+    for (int c = 0; c < nc; ++c) {
+      const int oc = G.box_octant[c0 + c];
+      __syncthreads();
+      for (int q = threadIdx.x; q < np; q += blockDim.x) {
+        const int mi = G.mi[q];
+        const int deg = (mi & 255) + ((mi >> 8) & 255) + ((mi >> 16) & 255);
+        va[q] = mom[((int64_t)(c0 + c) * ndp + d) * G.ms + q] / (T)(1 << deg);
       }
-      mom[((int64_t)P * ndp + d) * G.ms + b] = acc;
+      __syncthreads();
+      m2m_pass(G, np, 0, tab + ((oc & 1) ? P1 * P1 : 0), va, vb);
+      __syncthreads();
+      m2m_pass(G, np, 1, tab + ((oc & 2) ? P1 * P1 : 0), vb, va);
+      __syncthreads();
+      m2m_pass(G, np, 2, tab + ((oc & 4) ? P1 * P1 : 0), va, vb);
+      __syncthreads();
+      for (int q = threadIdx.x; q < np; q += blockDim.x) acc[q] += vb[q];
     }
+    __syncthreads();
+    for (int q = threadIdx.x; q < np; q += blockDim.x) mom[((int64_t)P * ndp + d) * G.ms + q] = acc[q];
   }
 }
 
 template <typename T>
-cudaError_t launch_m2m(const DevGeom& G, const int* parents, int n, const T* M2M, int ndp, T* mom, cudaStream_t st) {
+cudaError_t launch_m2m(const DevGeom& G, const int* parents, int n, int ndp, T* mom, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  k_m2m<T><<<n, 128, sizeof(T) * 8 * G.np, st>>>(G, parents, M2M, ndp, mom);
+  const size_t sm = sizeof(T) * (2 * (G.p + 1) * (G.p + 1) + 3 * G.np);
+  k_m2m<T><<<n, 128, sm, st>>>(G, parents, ndp, mom);
   return cudaGetLastError();
 }
 
@@ -193,35 +272,46 @@ cudaError_t launch_m2l_simt(const DevGeom& G, const DevTaskLists& L, const T* Tt
 }
 
 // ---------------------------------------------------------------- L2L
-// l_child[a] += sum_{b >= a} L[octant][a][b] l_parent[b]; stored transposed,
-// Lt[octant][b][a], for coalesced reads over a.  The parent's expansion has
-// its level's order, the child's is cut to its own (Sec. 4.3): a < nq_child.
+// One CTA per child box.  The parent's expansion has its level's order qp,
+// the child's is cut to its own (Sec. 4.3): the passes run over |b| <= qp,
+// the child receives |a| <= min(q_child, qp).
 template <typename T>
-__global__ void k_l2l(DevGeom G, const int* __restrict__ children, const T* __restrict__ L2L, int ndp,
-                      T* __restrict__ loc) {
+__global__ void k_l2l(DevGeom G, const int* __restrict__ children, int ndp, T* __restrict__ loc) {
   extern __shared__ unsigned char smraw[];
-  T* lp = reinterpret_cast<T*>(smraw);               // [np]
-  const int np = G.np;
+  const int P1 = G.p + 1;
+  T* tab = reinterpret_cast<T*>(smraw);              // [2][P+1][P+1]
+  T* va = tab + 2 * P1 * P1;                         // [np]
+  T* vb = va + G.np;                                 // [np]
+  shift_table(G, tab);
   const int C = children[blockIdx.x];
   const int P = G.box_parent[C];
-  const int nqc = nterms_q(G.box_q[C]), nqp = nterms_q(G.box_q[P]);
-  const T* Lm = L2L + (int64_t)G.box_octant[C] * np * np;
+  const int qp = G.box_q[P];
+  const int nqc = nterms_q(G.box_q[C]), nqp = nterms_q(qp);
+  const int oc = G.box_octant[C];
   for (int d = 0; d < ndp; ++d) {
     __syncthreads();
-    for (int i = threadIdx.x; i < nqp; i += blockDim.x) lp[i] = loc[((int64_t)P * ndp + d) * G.ms + i];
+    for (int q = threadIdx.x; q < nqp; q += blockDim.x) va[q] = loc[((int64_t)P * ndp + d) * G.ms + q];
     __syncthreads();
-    for (int a = threadIdx.x; a < nqc; a += blockDim.x) {
-      T acc = 0;
-      for (int b = a; b < nqp; ++b) acc += Lm[(int64_t)b * np + a] * lp[b];
-      loc[((int64_t)C * ndp + d) * G.ms + a] += acc;
+    l2l_pass(G, nqp, qp, 0, tab + ((oc & 1) ? P1 * P1 : 0), va, vb);
+    __syncthreads();
+    l2l_pass(G, nqp, qp, 1, tab + ((oc & 2) ? P1 * P1 : 0), vb, va);
+    __syncthreads();
+    l2l_pass(G, nqp, qp, 2, tab + ((oc & 4) ? P1 * P1 : 0), va, vb);
+    __syncthreads();
+    // a child of a higher order than its parent gets nothing above |a| = qp
+    for (int a = threadIdx.x; a < min(nqc, nqp); a += blockDim.x) {
+      const int mi = G.mi[a];
+      const int deg = (mi & 255) + ((mi >> 8) & 255) + ((mi >> 16) & 255);
+      loc[((int64_t)C * ndp + d) * G.ms + a] += vb[a] / (T)(1 << deg);
     }
   }
 }
 
 template <typename T>
-cudaError_t launch_l2l(const DevGeom& G, const int* children, int n, const T* L2L, int ndp, T* loc, cudaStream_t st) {
+cudaError_t launch_l2l(const DevGeom& G, const int* children, int n, int ndp, T* loc, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  k_l2l<T><<<n, 128, sizeof(T) * G.np, st>>>(G, children, L2L, ndp, loc);
+  const size_t sm = sizeof(T) * (2 * (G.p + 1) * (G.p + 1) + 2 * G.np);
+  k_l2l<T><<<n, 128, sm, st>>>(G, children, ndp, loc);
   return cudaGetLastError();
 }
 
@@ -975,11 +1065,11 @@ template cudaError_t launch_weights<float>(const DevGeom&, int, int64_t, const d
 template cudaError_t launch_weights<double>(const DevGeom&, int, int64_t, const double*, int64_t, int, int, double*, cudaStream_t);
 template cudaError_t launch_p2m<float>(const DevGeom&, const DevTaskLists&, const float*, int64_t, int, float*, cudaStream_t);
 template cudaError_t launch_p2m<double>(const DevGeom&, const DevTaskLists&, const double*, int64_t, int, double*, cudaStream_t);
-template cudaError_t launch_m2m<float>(const DevGeom&, const int*, int, const float*, int, float*, cudaStream_t);
-template cudaError_t launch_m2m<double>(const DevGeom&, const int*, int, const double*, int, double*, cudaStream_t);
+template cudaError_t launch_m2m<float>(const DevGeom&, const int*, int, int, float*, cudaStream_t);
+template cudaError_t launch_m2m<double>(const DevGeom&, const int*, int, int, double*, cudaStream_t);
 template cudaError_t launch_m2l_simt<float>(const DevGeom&, const DevTaskLists&, const float*, int, const float*, float*, cudaStream_t, const int*, int);
 template cudaError_t launch_m2l_simt<double>(const DevGeom&, const DevTaskLists&, const double*, int, const double*, double*, cudaStream_t, const int*, int);
-template cudaError_t launch_l2l<float>(const DevGeom&, const int*, int, const float*, int, float*, cudaStream_t);
-template cudaError_t launch_l2l<double>(const DevGeom&, const int*, int, const double*, int, double*, cudaStream_t);
+template cudaError_t launch_l2l<float>(const DevGeom&, const int*, int, int, float*, cudaStream_t);
+template cudaError_t launch_l2l<double>(const DevGeom&, const int*, int, int, double*, cudaStream_t);
 
 }  // namespace bcfmm

@@ -97,8 +97,8 @@ struct TaylorArgs {
 template <int Q>
 __global__ void __launch_bounds__(128) k_m2l_taylor(TaylorArgs A) {
   constexpr int NQ = (Q + 1) * (Q + 2) * (Q + 3) / 6;
-  // 32-byte loads up to order 5; 16-byte loads above (fewer live registers)
-  constexpr int W = Q <= 5 ? 8 : 4;
+  // 32-byte loads up to order 6; 16-byte loads above (fewer live registers)
+  constexpr int W = Q <= 6 ? 8 : 4;
   constexpr int NV = (NQ + W - 1) / W;
   const int w = blockIdx.x * 4 + (threadIdx.x >> 5), lane = threadIdx.x & 31, d = blockIdx.y;
   if (w >= A.nwarp) return;
