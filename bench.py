@@ -658,6 +658,11 @@ def run_largest(args):
         data = {"P": (duP(bq, nrm[:, None]).mean(1)[None], uP(bq).mean(1)[None], uP(tq).mean(1)),
                 "L": (duL(bq, nrm[:, None]).mean(1)[None], uL(bq).mean(1)[None], uL(tq).mean(1))}
         vol = _sizes(m.verts, m.tets)
+        # boundary tets (a face on the cube's surface, the set B_L of Sec. 2):
+        # the BC mesh has size h there, while interior cells stay coarse
+        tv = m.verts[m.tets]
+        onb = (np.abs(tv) < 1e-12) | (np.abs(tv - 1.0) < 1e-12)
+        bnd = (onb.sum(1) >= 3).any(1)
         t0 = time.perf_counter()
         ctx = bcfmm.Context.from_mesh(m, stream=stream, **prm)
         setup = time.perf_counter() - t0
@@ -679,10 +684,14 @@ def run_largest(args):
         green = {}
         num = (u["vtv"] + u["btv"]) / vol
         green["poisson_vtv_btv"] = float(np.linalg.norm(num - data["P"][2]) / np.linalg.norm(data["P"][2]))
+        green["poisson_vtv_btv_boundary_tets"] = float(np.linalg.norm((num - data["P"][2])[bnd]) /
+                                                       np.linalg.norm(data["P"][2][bnd]))
         ctx.set_density(bcfmm.BOUNDARY, data["L"][0])
         ctx.set_density(bcfmm.DIPOLE, data["L"][1])
         numL = ctx.eval_btv().cpu().numpy()[0] / vol
         green["laplace_btv"] = float(np.linalg.norm(numL - data["L"][2]) / np.linalg.norm(data["L"][2]))
+        green["laplace_btv_boundary_tets"] = float(np.linalg.norm((numL - data["L"][2])[bnd]) /
+                                                   np.linalg.norm(data["L"][2][bnd]))
         # the single layer alone against direct sampling (the double layer's
         # discrete operator has no sampling counterpart)
         ctx.clear_dipole()
@@ -707,7 +716,7 @@ def run_largest(args):
         del outs
         torch.cuda.empty_cache()
     rates = {}
-    for k in ("poisson_vtv_btv", "laplace_btv"):
+    for k in ("poisson_vtv_btv", "laplace_btv", "poisson_vtv_btv_boundary_tets", "laplace_btv_boundary_tets"):
         e = [lv["green_rel_l2_vs_analytic"][k] for lv in levels]
         rates[k] = {"errors": e, "observed_orders": [float(math.log2(e[i] / e[i + 1])) for i in range(len(e) - 1)]}
     big = levels[-1]

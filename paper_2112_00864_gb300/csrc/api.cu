@@ -838,13 +838,9 @@ static int build_impl(const double* verts, const int64_t* vert_off, const int32_
       }
     }
     if (prm.precision == BCFMM_FP32) {
-      // Taylor-form M2L: D^gamma G(o), |gamma| <= the largest order among
-      // the levels that the register-blocked kernel takes
+      // Taylor-form M2L: D^gamma G(o), |gamma| <= the largest order of any level
       int qt = 0;
-      for (int l = 0; l < C->nlevels; ++l) {
-        const int q = level_order(prm, l);
-        if (q <= kTaylorMaxQ) qt = std::max(qt, q);
-      }
+      for (int l = 0; l < C->nlevels; ++l) qt = std::max(qt, level_order(prm, l));
       if (qt > 0) {
         const int pitch = m2l_taylor_pitch(qt);
         std::vector<float> g((size_t)std::max(ncode, 1) * pitch, 0.f);
@@ -1365,8 +1361,7 @@ static int eval_impl(bcfmm_ctx* C, int t, double* out, int out_is_device, bool s
       CU(launch_m2l_tc(G, L, D.tcs, C->tc, ndp, C->mom32, C->loc32, C->tc_partial, C->tc_momb, st));
       if (D.tcs.nsimt > 0) CU(launch_m2l_simt<float>(G, L, C->T32, ndp, C->mom32, C->loc32, st, D.tcs.simt_sel, D.tcs.nsimt));
     } else if (C->ty.g) {
-      CU(launch_m2l_taylor(G, D.tys, C->ty, ndp, C->mom32, C->loc32, C->ty_momp, C->ty_partial, st));
-      if (D.tys.nsimt > 0) CU(launch_m2l_simt<float>(G, L, C->T32, ndp, C->mom32, C->loc32, st, D.tys.simt_sel, D.tys.nsimt));
+      CU(launch_m2l_taylor(G, L, D.tys, C->ty, ndp, C->mom32, C->loc32, C->ty_momp, C->ty_partial, st));
     } else {
       CU(launch_m2l_simt<float>(G, L, C->T32, ndp, C->mom32, C->loc32, st));
     }
@@ -1515,8 +1510,7 @@ extern "C" int bcfmm_eval_noalloc(bcfmm_ctx* C, int32_t task, const double* dens
     CU(launch_m2l_tc(G, L, D.tcs, C->tc, ndp, C->mom32, C->loc32, partial, C->tc_momb, st));
     if (D.tcs.nsimt > 0) CU(launch_m2l_simt<float>(G, L, C->T32, ndp, C->mom32, C->loc32, st, D.tcs.simt_sel, D.tcs.nsimt));
   } else if (C->ty.g) {
-    CU(launch_m2l_taylor(G, D.tys, C->ty, ndp, C->mom32, C->loc32, C->ty_momp, reinterpret_cast<float*>(partial), st));
-    if (D.tys.nsimt > 0) CU(launch_m2l_simt<float>(G, L, C->T32, ndp, C->mom32, C->loc32, st, D.tys.simt_sel, D.tys.nsimt));
+    CU(launch_m2l_taylor(G, L, D.tys, C->ty, ndp, C->mom32, C->loc32, C->ty_momp, reinterpret_cast<float*>(partial), st));
   } else {
     CU(launch_m2l_simt<float>(G, L, C->T32, ndp, C->mom32, C->loc32, st));
   }

@@ -158,6 +158,71 @@ __global__ void __launch_bounds__(128) k_m2l_taylor_reduce(int ntgt, const int* 
   loc[((int64_t)tb * ndp + d) * ms + a] = (hi + lo) * post[a] / (float)box_cs[tb].w;
 }
 
+// Orders above the register-blocked range (any q <= p): one CTA per target,
+// the entry's g row and prescaled moment row staged in shared memory, one
+// thread per output a (strided), the multi-index of a + b computed from the
+// components; FP32 products per entry, compensated FP32 sum over the list.
+template <int ND>
+__global__ void __launch_bounds__(128) k_m2l_taylor_wide(DevGeom G, DevTaskLists L, const int* __restrict__ sel,
+                                                        const float* __restrict__ g, int pitch,
+                                                        const float* __restrict__ momp, const float* __restrict__ post,
+                                                        float* __restrict__ loc) {
+  constexpr int ndp = ND;
+  extern __shared__ float wsm[];
+  const int ki = sel[blockIdx.x];
+  const int tb = L.m2l_tgt[ki];
+  const int q = G.box_q[tb], nq = nterms_q(q);
+  float* sg = wsm;                       // [nq] the entry's g row
+  float* smv = sg + pitch;               // [ndp][nq] its prescaled moment rows
+  int* smi = reinterpret_cast<int*>(smv + (size_t)ndp * pitch);   // [nq] packed multi-indices
+  for (int i = threadIdx.x; i < nq; i += blockDim.x) smi[i] = G.mi[i];
+  constexpr int kMaxPer = 4;             // outputs per thread: nq <= 4 * 128 (q <= 12)
+  constexpr int kMaxD = ND;
+  float hi[kMaxPer][kMaxD], lo[kMaxPer][kMaxD];
+#pragma unroll
+  for (int u = 0; u < kMaxPer; ++u)
+#pragma unroll
+    for (int d = 0; d < kMaxD; ++d) hi[u][d] = lo[u][d] = 0.f;
+  const int e0 = L.vl_off[ki], e1 = L.vl_off[ki + 1];
+  for (int e = e0; e < e1; ++e) {
+    const int sb = L.vl_src[e];
+    const float* gr = g + (int64_t)L.vl_code[e] * pitch;
+    __syncthreads();
+    for (int i = threadIdx.x; i < nq; i += blockDim.x) sg[i] = gr[i];
+    for (int i = threadIdx.x; i < ndp * nq; i += blockDim.x)
+      smv[(i / nq) * pitch + i % nq] = momp[((int64_t)sb * ndp + i / nq) * pitch + i % nq];
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < kMaxPer; ++u) {
+      const int a = threadIdx.x + u * 128;
+      if (a >= nq) break;
+      const int ma = smi[a];
+      const int ai = ma & 255, aj = (ma >> 8) & 255, ak = (ma >> 16) & 255;
+      const int kb = nterms_q(q - ai - aj - ak);
+      float part[kMaxD];
+#pragma unroll
+      for (int d = 0; d < kMaxD; ++d) part[d] = 0.f;
+      for (int b = 0; b < kb; ++b) {
+        const int mb = smi[b];
+        const int gi = ai + (mb & 255), gj = aj + ((mb >> 8) & 255), gk = ak + ((mb >> 16) & 255);
+        const int dg = gi + gj + gk;
+        const float gv = sg[dg * (dg + 1) * (dg + 2) / 6 + (gj + gk) * (gj + gk + 1) / 2 + gk];
+#pragma unroll
+        for (int d = 0; d < kMaxD; ++d) part[d] = fmaf(gv, smv[d * pitch + b], part[d]);
+      }
+#pragma unroll
+      for (int d = 0; d < kMaxD; ++d) two_sum(hi[u][d], lo[u][d], part[d]);
+    }
+  }
+  const float inv_s = 1.0f / (float)G.box_cs[tb].w;
+#pragma unroll
+  for (int u = 0; u < kMaxPer; ++u) {
+    const int a = threadIdx.x + u * 128;
+    if (a >= nq) break;
+    for (int d = 0; d < ndp; ++d) loc[((int64_t)tb * ndp + d) * G.ms + a] = (hi[u][d] + lo[u][d]) * post[a] * inv_s;
+  }
+}
+
 template <int Q>
 cudaError_t launch_order(const TaylorOrderSched& O, const TaylorTaskSched& S, const TaylorTables& tab, const DevGeom& G,
                          int ndp, const float* momp, float* loc, float* partial, cudaStream_t st) {
@@ -250,18 +315,33 @@ bool m2l_taylor_schedule(const std::vector<int>& m2l_tgt, const std::vector<int>
   return true;
 }
 
-cudaError_t launch_m2l_taylor(const DevGeom& G, const TaylorTaskSched& S, const TaylorTables& tab, int ndp,
-                              const float* mom, float* loc, float* momp, float* partial, cudaStream_t st) {
+cudaError_t launch_m2l_taylor(const DevGeom& G, const DevTaskLists& L, const TaylorTaskSched& S,
+                              const TaylorTables& tab, int ndp, const float* mom, float* loc, float* momp,
+                              float* partial, cudaStream_t st) {
   int qtop = 0;
   for (int q = 1; q <= kTaylorMaxQ; ++q)
     if (S.ord[q].nwarp > 0) qtop = q;
-  if (qtop == 0) return cudaSuccess;
-  if (qtop > tab.q || tab.gpitch != m2l_taylor_pitch(tab.q)) return cudaErrorInvalidValue;
+  if (qtop == 0 && S.nsimt == 0) return cudaSuccess;
+  if (qtop > tab.q || tab.gpitch != m2l_taylor_pitch(tab.q) || ndp > 16 || tab.q > 12) return cudaErrorInvalidValue;
   {
     const int64_t nrow = (int64_t)G.nbox * ndp;
     const int64_t n = nrow * tab.gpitch;
-    k_taylor_prescale<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(mom, nrow, G.ms, nterms_q(qtop), tab.gpitch, tab.fac,
-                                                                   momp);
+    k_taylor_prescale<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(mom, nrow, G.ms, nterms_q(tab.q), tab.gpitch,
+                                                                   tab.fac, momp);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (S.nsimt > 0) {
+    const size_t sm = sizeof(float) * (size_t)(1 + ndp) * tab.gpitch + sizeof(int) * tab.gpitch;
+    const float* post = tab.fac + tab.gpitch;
+    switch (ndp) {
+      case 1: k_m2l_taylor_wide<1><<<S.nsimt, 128, sm, st>>>(G, L, S.simt_sel, tab.g, tab.gpitch, momp, post, loc); break;
+      case 2: k_m2l_taylor_wide<2><<<S.nsimt, 128, sm, st>>>(G, L, S.simt_sel, tab.g, tab.gpitch, momp, post, loc); break;
+      case 4: k_m2l_taylor_wide<4><<<S.nsimt, 128, sm, st>>>(G, L, S.simt_sel, tab.g, tab.gpitch, momp, post, loc); break;
+      case 8: k_m2l_taylor_wide<8><<<S.nsimt, 128, sm, st>>>(G, L, S.simt_sel, tab.g, tab.gpitch, momp, post, loc); break;
+      case 16: k_m2l_taylor_wide<16><<<S.nsimt, 128, sm, st>>>(G, L, S.simt_sel, tab.g, tab.gpitch, momp, post, loc); break;
+      default: return cudaErrorInvalidValue;
+    }
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

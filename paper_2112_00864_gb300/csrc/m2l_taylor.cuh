@@ -10,8 +10,8 @@
 
 namespace bcfmm {
 
-// Largest order handled by the register-blocked kernel (higher orders go to
-// the generic kernel with the full T_o table).
+// Largest order handled by the register-blocked kernel (higher orders, up
+// to 12, go to a one-CTA-per-target kernel in the same Taylor form).
 constexpr int kTaylorMaxQ = 7;
 
 // The expansion coefficients of Sec. 3.3,
@@ -46,7 +46,7 @@ struct TaylorTaskSched {
   int cbits = 0;                           // bits of the offset code in pk
   size_t partial_per_dens = 0;             // floats of chunk partial sums per density
   const int* simt_sel = nullptr;           // targets (indices into the task's list) of
-  int nsimt = 0;                           // higher orders: generic kernel
+  int nsimt = 0;                           // higher orders: one CTA per target
 };
 
 // Host side of one order's schedule (built at setup, uploaded by the caller).
@@ -80,7 +80,10 @@ int m2l_taylor_pitch(int q);
 // Scratch (device memory owned by the caller):
 //   momp:    nbox * ndp * m2l_taylor_pitch(tab.q) floats (prescaled moments)
 //   partial: ndp * S.partial_per_dens floats (chunk sums)
-cudaError_t launch_m2l_taylor(const DevGeom& G, const TaylorTaskSched& S, const TaylorTables& tab, int ndp,
-                              const float* mom, float* loc, float* momp, float* partial, cudaStream_t st);
+// tab.q must be the largest order of any target (the wide kernel reads the
+// g rows and moments up to it); targets in S.simt_sel use the wide kernel.
+cudaError_t launch_m2l_taylor(const DevGeom& G, const DevTaskLists& L, const TaylorTaskSched& S,
+                              const TaylorTables& tab, int ndp, const float* mom, float* loc, float* momp,
+                              float* partial, cudaStream_t st);
 
 }  // namespace bcfmm
