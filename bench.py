@@ -60,6 +60,12 @@ def workload():
 CHOSEN = dict(p=7, q0=6, eta0=0.6, leaf_size=128, precision="fp32")
 PLAIN = dict(p=7, q0=6, eta0=0.6, leaf_size=128, precision="fp64")
 SAMPLE_TARGETS = 1024      # per task, for the accuracy gate and the CPU baseline
+# DRAM bytes (read + write) of one launch of each reported kernel on this
+# workload, from ncu --set full captures of VtV's launch under
+# "--workload kernels"; they hold for the kernels as captured and are to be
+# re-taken when a kernel changes
+NCU_TRAFFIC = {"k_p2p_l2p_f32x2": (44.95e6, "ncu capture, VtV launch"),
+               "k_m2l_taylor": (61.15e6, "ncu capture, VtV's order-6 launch")}
 
 
 def dist_env():
@@ -180,6 +186,19 @@ def oracle_sample(m, f, tv, tb):
     uv = O.direct("vtv", m, f, targets=tv, nthreads=cores)[0]
     ub = O.direct("vtb", m, f, targets=tb, nthreads=cores)[0]
     return uv, ub, time.perf_counter() - t0, cores
+
+
+def near_rule_gap(m, f, tv, cores):
+    """How far the discrete operator's default near rule (near_n = 3,
+    near_k = 1) sits from an accurate evaluation of the touching pairs'
+    Galerkin integrals A_ts: O1 with the default rule against O1 with a
+    refined rule (5 nodes per direction, 2 refinements: 64x the outer
+    points) on a few sampled VtV targets (rel L2 of the cell averages)."""
+    import oracle as O
+    t0 = time.perf_counter()
+    a = O.direct("vtv", m, f, targets=tv, nthreads=cores)[0]
+    b = O.direct("vtv", m, f, targets=tv, n=5, k=2, nthreads=cores)[0]
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b)), len(tv), time.perf_counter() - t0
 
 
 def rel_err(u, ref, size):
@@ -318,6 +337,7 @@ def run_ours(args):
     if rank == 0:
         tv, tb = sample_targets(m)
         ov, ob, osec, cores = oracle_sample(m, f, tv, tb)
+        gap, ngap, gsec = near_rule_gap(m, f, tv[::64], cores)
         err = {"vtv": rel_err(u_v[tv], ov, vol[tv]), "vtb": rel_err(u_b[tb], ob, area[tb])}
         err_plain = {"vtv": rel_err(plain_v[tv], ov, vol[tv]), "vtb": rel_err(plain_b[tb], ob, area[tb])}
         pk, src = peaks()
@@ -338,7 +358,8 @@ def run_ours(args):
         # box pairs of each order times 2 C(q+6, 6): one FMA per (a, b) with |a| + |b| <= q
         m2l_flop = sum(2.0 * math.comb(q + 6, 6) * n for q, n in enumerate(st["vtv"]["m2l_pairs_by_order"]))
         roof_p2p = {"kernel": "k_p2p_l2p_f32x2", "bound": "alu", "achieved": ops_p2p / (p2p_ms * 1e-3) / 1e12,
-                    "peak": fp32_peak / 1e12, "unit": "TFLOP/s", "traffic": None,
+                    "peak": fp32_peak / 1e12, "unit": "TFLOP/s", "traffic": NCU_TRAFFIC["k_p2p_l2p_f32x2"][0],
+                    "traffic_source": NCU_TRAFFIC["k_p2p_l2p_f32x2"][1],
                     "note": f"FP32-pipe ops (7 per pair: 3 sub, 1 mul, 2 fma, 1 fma) per s vs {nsm} SMs x 128 "
                             "lanes x max SM clock; the rsqrt on MUFU caps it at 7/8 of this peak",
                     "ms_per_step": float(p2p_ms), "pairs": int(pairs),
@@ -357,7 +378,9 @@ def run_ours(args):
         else:
             roof_m2l = {"kernel": "k_m2l_taylor" if CHOSEN["precision"] == "fp32" else "k_m2l_simt", "bound": "alu",
                         "achieved": m2l_flop / (m2l_ms * 1e-3) / 1e12,
-                        "peak": 2 * fp32_peak / 1e12, "unit": "TFLOP/s", "traffic": None,
+                        "peak": 2 * fp32_peak / 1e12, "unit": "TFLOP/s",
+                        "traffic": NCU_TRAFFIC["k_m2l_taylor"][0] if CHOSEN["precision"] == "fp32" else None,
+                        "traffic_source": NCU_TRAFFIC["k_m2l_taylor"][1],
                         "note": "algorithmic flops 2*C(q+6,6) per box pair of order q (one FMA per (a, b), "
                                 "|a|+|b| <= q) over the whole M2L stage (prescale, chunk sums, reduce) vs FP32 "
                                 "FMA peak (2 flops x 128 lanes x SMs x max SM clock)",
@@ -380,7 +403,11 @@ def run_ours(args):
             "accuracy": {"rel_l2_vs_oracle": {k: v[0] for k, v in err.items()},
                          "rel_max_vs_oracle": {k: v[1] for k, v in err.items()},
                          "sample_targets_per_task": SAMPLE_TARGETS,
-                         "ok": acc_ok},
+                         "ok": acc_ok,
+                         "reference": "O1: the discrete operator (product rule for far element pairs, the "
+                                      "near rule near_n = 3, near_k = 1 for near pairs), not the exact A_ts",
+                         "near_rule_gap_vtv": {"rel_l2_default_vs_refined_near_rule": gap, "targets": ngap,
+                                               "seconds": gsec}},
             "plain_fp64": {"value": npts / (plain_ms * 1e-3), "ms_per_step": plain_ms,
                            "rel_l2_vs_oracle": {k: v[0] for k, v in err_plain.items()},
                            "chosen_over_plain": plain_ms / ms},
