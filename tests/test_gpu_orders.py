@@ -122,7 +122,8 @@ def test_taylor_orders_against_fp64(bc, c1, prec):
     this bound: the boundary density's far field is dominated by the
     orders the split represents least well; it is not a chosen form.)"""
     m, f, g = c1
-    for p, sched in ((7, [0, 0, 7, 6, 5, 4, 3, 2]), (7, [0, 0, 1, 2, 3, 4, 5, 7]), (9, [0, 0, 9, 8, 7, 6, 5, 4])):
+    for p, sched in ((7, [0, 0, 7, 6, 5, 4, 3, 2]), (7, [0, 0, 1, 2, 3, 4, 5, 7]), (7, [0, 0, 4, 4, 4, 4]),
+                     (9, [0, 0, 9, 8, 7, 6, 5, 4])):
         legs = (("vtv", f, bc.VOLUME), ("vtb", f, bc.VOLUME)) + ((("btv", g, bc.BOUNDARY),) if prec == "fp32" else ())
         for task, dens, kind in legs:
             u = {}
