@@ -3,10 +3,11 @@ accuracy target on the caller's own meshes and densities.
 
 Search space (all of it is cheap to try because ``Context.build_like``
 copies the near pairs and their FP64 corrections instead of recomputing
-them): leaf size, expansion order p with the precisions the tensor-core M2L
-allows for it (BF16 hi+lo split for p <= 7, hi+mid+lo for p <= 6, FP32 on
-CUDA cores above),
-and the tensor-core work-unit size ("tile" of the M2L launch: interaction
+them): leaf size, the box-neighbour parameter eta0 (Eq. def:neighbors: the
+near-field / interaction-list trade-off), the level-order schedule
+q_l = min(p, q0 + L - l) of Sec. 4.3, and the M2L form: FP32 Taylor form on
+CUDA cores, or the tensor-core BF16 hi+lo split (orders <= 6 on the tensor
+cores) with its work-unit size ("tile" of the M2L launch: interaction
 entries per CTA).  Each candidate is timed with CUDA events as the graph
 launch a user makes (``Context.eval_graph``) and its error is measured on
 sampled target elements against the library's FP64 direct evaluation of
@@ -24,7 +25,8 @@ import numpy as np
 
 from . import bcfmm
 
-DEFAULT_SPACE = dict(leaf_size=(32, 64, 128), p=(4, 5, 6, 7, 8), tc_unit=(0, 32))
+DEFAULT_SPACE = dict(leaf_size=(64, 128), eta0=(0.5, 0.6, 0.7), q0=(4, 5, 6, 7), p=7,
+                     tc_space=dict(eta0=(0.5,), q0=(4, 5), tc_unit=(0, 32)))
 
 
 @dataclass
@@ -36,23 +38,18 @@ class Trial:
     note: str = ""
 
 
-def _precisions_for(p: int):
-    """Precisions the tensor-core M2L offers at order p: the 2-term BF16
-    split up to p = 7, the 3-term split up to p = 6; FP32 on CUDA cores
-    above."""
-    if p <= 6:
-        return ("bf16x2", "bf16x3")
-    return ("bf16x2",) if p <= 7 else ("fp32",)
-
-
 def candidates(space: dict | None = None):
+    """FP32 Taylor-form candidates over leaf x eta0 x q0, then the
+    tensor-core ones over leaf x the (smaller) tc_space."""
     space = dict(DEFAULT_SPACE, **(space or {}))
+    p = int(space["p"])
     out = []
-    for ls, p in itertools.product(space["leaf_size"], space["p"]):
-        for prec in _precisions_for(p):
-            units = space["tc_unit"] if prec == "bf16x2" else (0,)
-            for u in units:
-                out.append(dict(leaf_size=int(ls), p=int(p), precision=prec, tc_unit=int(u)))
+    for ls, eta0, q0 in itertools.product(space["leaf_size"], space["eta0"], space["q0"]):
+        out.append(dict(leaf_size=int(ls), eta0=float(eta0), q0=int(q0), p=p, precision="fp32"))
+    tcs = space.get("tc_space") or {}
+    for ls, eta0, q0, u in itertools.product(space["leaf_size"], tcs.get("eta0", ()), tcs.get("q0", ()),
+                                             tcs.get("tc_unit", (0,))):
+        out.append(dict(leaf_size=int(ls), eta0=float(eta0), q0=int(q0), p=p, precision="bf16x2", tc_unit=int(u)))
     return out
 
 

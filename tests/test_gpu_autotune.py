@@ -67,10 +67,10 @@ def test_autotune_pick_meets_tolerance(bc):
     F = np.concatenate([densities(m, "bumps", ndens=2, seed=i)[0] for i, m in enumerate(meshes)], axis=1)
     base = bc.Context.from_meshes(meshes, p=4, precision="fp32")
     tol = 1e-6
-    space = dict(leaf_size=(32, 128), p=(4, 6, 8), tc_unit=(0, 16))
+    space = dict(leaf_size=(32, 128), eta0=(0.5, 0.7), q0=(3, 6), tc_space=dict(eta0=(0.5,), q0=(4,), tc_unit=(0, 16)))
     best, trials = autotune(base, F, tasks=("vtv", "vtb"), tol=tol, space=space, nsample=48, reps=3)
-    # per leaf size: p = 4, 6 with bf16x2 (2 unit sizes) and bf16x3, p = 8 with fp32
-    assert len(trials) == 2 * (2 * 3 + 1)
+    # per leaf size: FP32 Taylor form over eta0 x q0 (2 x 2), tensor cores 1 x 1 x 2 units
+    assert len(trials) == 2 * (2 * 2 + 2)
     chosen = [t for t in trials if t.params == best][0]
     assert chosen.ok and chosen.ms == min(t.ms for t in trials if t.ok)
     # the pick against the oracle's O1 on sampled targets of every mesh

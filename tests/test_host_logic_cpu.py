@@ -8,16 +8,14 @@ from paper_2112_00864_gb300 import autotune as A
 from paper_2112_00864_gb300 import bcfmm, learned
 
 
-def test_candidates_follow_tensor_core_limits():
+def test_candidates_cover_eta0_and_order_schedule():
     c = A.candidates()
-    assert len(c) == 3 * (3 * 3 + 2 + 1)          # leaf x {p4..6: x2 (2 units) + x3, p7: x2 (2 units), p8: fp32}
-    for t in c:
-        if t["precision"] == "bf16x3":
-            assert t["p"] <= 6 and t["tc_unit"] == 0
-        if t["precision"] == "bf16x2":
-            assert t["p"] <= 7
-        if t["p"] == 8:
-            assert t["precision"] == "fp32"
+    # FP32 Taylor form: 2 leaves x 3 eta0 x 4 q0; tensor cores: 2 leaves x 1 eta0 x 2 q0 x 2 units
+    assert len(c) == 2 * 3 * 4 + 2 * 1 * 2 * 2
+    fp32 = [t for t in c if t["precision"] == "fp32"]
+    assert {t["eta0"] for t in fp32} == {0.5, 0.6, 0.7} and {t["q0"] for t in fp32} == {4, 5, 6, 7}
+    assert all(t["p"] == 7 for t in c)
+    assert all("tc_unit" in t for t in c if t["precision"] == "bf16x2")
 
 
 class _Out:
@@ -29,6 +27,10 @@ class _Out:
 
     def numpy(self):
         return self.a
+
+
+def _key(c):
+    return (c["precision"], c["leaf_size"], c["eta0"], c["q0"], c.get("tc_unit", 0))
 
 
 class _FakeCtx:
@@ -51,8 +53,7 @@ class _FakeCtx:
         return np.ones((1, len(idx))) * size
 
     def build_like(self, **kw):
-        key = (kw["p"], kw["precision"], kw["leaf_size"], kw["tc_unit"])
-        return _FakeCtx(self.errs, dict(kw, key=key))
+        return _FakeCtx(self.errs, dict(kw, key=_key(kw)))
 
     def eval_graph(self, tasks, outs=None):
         e = self.errs[self.params["key"]]
@@ -68,22 +69,25 @@ class _FakeCtx:
 
 
 def test_autotune_picks_fastest_within_the_margin():
-    space = dict(leaf_size=(64, 128), p=(4, 6, 8), tc_unit=(0,))
+    space = dict(leaf_size=(64, 128), eta0=(0.5, 0.7), q0=(4, 6),
+                 tc_space=dict(eta0=(0.5,), q0=(4,), tc_unit=(0,)))
     cands = A.candidates(space)
-    err = {4: 3e-5, 6: 4.9e-7, 8: 1e-7}
-    errs = {(c["p"], c["precision"], c["leaf_size"], c["tc_unit"]): err[c["p"]] * (1.2 if c["precision"] == "bf16x2"
-                                                                                    else 1.0) for c in cands}
-    ms = {4: 1.0, 6: 2.0, 8: 9.0}
+    # error: looser eta0 and lower q0 cost accuracy; time: looser eta0 is faster
+    def e_of(c):
+        e = {4: 4e-7, 6: 1e-7}[c["q0"]] * (3.0 if c["eta0"] == 0.7 else 1.0)
+        return e * (1.5 if c["precision"] == "bf16x2" else 1.0)
+    errs = {_key(c): e_of(c) for c in cands}
 
     def timer(ctx, tasks, reps):
         p = ctx.params
-        return ms[p["p"]] * (1.5 if p["precision"] == "bf16x3" else 1.0) * (0.9 if p["leaf_size"] == 128 else 1.0)
+        t = (1.0 if p["eta0"] == 0.7 else 2.0) * (1.3 if p["q0"] == 6 else 1.0)
+        return t * (0.8 if p["precision"] == "bf16x2" else 1.0) * (0.9 if p["leaf_size"] == 128 else 1.0)
 
     best, trials = A.autotune(_FakeCtx(errs), np.ones((1, 40)), tol=1e-6, space=space, timer=timer, nsample=16)
-    # p = 6 bf16x2 (5.9e-7) misses the 0.5e-6 margin; p = 6 bf16x3 (4.9e-7) is the fastest that passes
-    assert best == dict(leaf_size=128, p=6, precision="bf16x3", tc_unit=0), best
-    assert all(abs(t.err["vtv"] - errs[(t.params["p"], t.params["precision"], t.params["leaf_size"], 0)]) < 1e-12
-               for t in trials)
+    # eta0 0.7 with q0 6 (3e-7) is within 0.5e-6 and the fastest that passes; the
+    # tensor-core candidate (6e-7) and eta0 0.7 with q0 4 (1.2e-6) miss the margin
+    assert best == dict(leaf_size=128, eta0=0.7, q0=6, p=7, precision="fp32"), best
+    assert all(abs(t.err["vtv"] - errs[_key(t.params)]) < 1e-12 for t in trials)
     with pytest.raises(RuntimeError):
         A.autotune(_FakeCtx({k: 1e-3 for k in errs}), np.ones((1, 40)), tol=1e-6, space=space, timer=timer, nsample=16)
 
