@@ -14,17 +14,21 @@ the dominant kernel (live CUDA events on the library's stream) and the CPU
 oracle's throughput on a bounded sample (cpu_baseline).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload ball|batch|learned]
+                  [--workload ball|batch|learned|largest|kernels]
 
 --workload batch: 64 ragged cube/ball BC meshes (h in {1/8, 1/16, 1/32}),
 4 Gaussian-bump densities each, one forest, one graph launch per step, the
 configuration picked by the autotuner on a sample of the meshes.
---workload largest: unit cube h = 1/32, 1/64, 1/128, VtV + VtB + BtV at
-p = 8 with the learned near field, accuracy per h and observed convergence.
+--workload largest: unit cube h = 1/32, 1/64, 1/128, VtV + VtB + BtV with
+the double layer, orders capped at p = 8, the learned near field; accuracy
+per h against the discrete operator and the Green representations of Sec. 5
+against the analytic solutions, with the observed orders across h.
 --workload learned: unit cube h = 1/64; the near-singular correction
 network trained on random BC meshes, then the build with the learned
 correction against the build with the FP64 near rule (setup time, learned
 fraction, accuracy against the oracle, throughput).
+--workload kernels: the ball workload's chosen form task by task, no oracle
+and no baselines (the command profilers wrap).
 """
 from __future__ import annotations
 
