@@ -568,13 +568,49 @@ __global__ void __launch_bounds__(128) k_p2p_l2p_f32(DevGeom G, DevTaskLists L, 
 
 
 
+// The packed pair loop over pairs [k0, k1) of a staged tile: per pair and
+// target, three packed subtractions (the sources are stored negated), the
+// packed r^2 (one multiply, two FMAs), two rsqrt and one packed FMA per
+// density.  CHECK: the tile holds the target points themselves (r^2 = 0).
+template <int ND, int TPT, bool CHECK>
+__device__ __forceinline__ void p2p_pairs_x2(const float4* __restrict__ xy, const float4* __restrict__ zw,
+                                             const float2* __restrict__ w2, int k0, int k1, const float2 (&X)[TPT],
+                                             const float2 (&Y)[TPT], const float2 (&Z)[TPT], float2 (&acc)[TPT][ND]) {
+#pragma unroll 4
+  for (int k = k0; k < k1; ++k) {
+    const float4 a = xy[k], c = zw[k];
+    const float2 nx = make_float2(a.x, a.y), ny = make_float2(a.z, a.w), nz = make_float2(c.x, c.y);
+    const float2 w0 = make_float2(c.z, c.w);
+    float2 wb = w0;
+    if constexpr (ND > 1) wb = w2[k];
+#pragma unroll
+    for (int u = 0; u < TPT; ++u) {
+      const float2 dx = __fadd2_rn(X[u], nx), dy = __fadd2_rn(Y[u], ny), dz = __fadd2_rn(Z[u], nz);
+      const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+      float2 ri;
+      if constexpr (CHECK) ri = make_float2(r2.x > 0.f ? rsqrt_ftz(r2.x) : 0.f, r2.y > 0.f ? rsqrt_ftz(r2.y) : 0.f);
+      else ri = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
+      acc[u][0] = __ffma2_rn(w0, ri, acc[u][0]);
+      if constexpr (ND > 1) acc[u][ND - 1] = __ffma2_rn(wb, ri, acc[u][ND - 1]);
+    }
+  }
+}
+
 // Packed form for ND <= 2: TPT targets per thread (4 for one density, 2
-// for two) and source points taken two at a time, every arithmetic instruction on a float2 (the two sources
-// of a pair: __fadd2_rn / __fmul2_rn / __ffma2_rn), so a target keeps two
-// independent partial sums and the instructions issued per point pair
-// nearly halve.  Source coordinates are staged negated in shared memory
-// (x_t + (-y) needs no separate negation); an odd tile is padded with a
-// weightless point at -1e30, whose distance overflows to inf (rsqrt 0).
+// for two) and source points taken two at a time, every arithmetic
+// instruction on a float2 (the two sources of a pair: __fadd2_rn /
+// __fmul2_rn / __ffma2_rn), so a target keeps two independent partial sums
+// and the instructions issued per point pair nearly halve.  A tile of
+// source points is staged pair-interleaved in shared memory, negated and
+// relative to the target leaf's centre: xy[k] = (x0, x1, y0, y1), zw[k] =
+// (z0, z1, w0, w1) for the pair k = (2k, 2k + 1), so one pair costs two
+// 16-byte shared loads.  Each of the NG thread groups takes a contiguous
+// range of pairs (odd length, so two groups' loads in one quarter-warp fall
+// in different banks) walked with unit stride.  An odd tile is padded with a
+// weightless point at -1e30, whose distance overflows to inf (rsqrt 0).  Only
+// the pairs that hold the leaf's own points (the first run of a VtV list)
+// select r^2 = 0 out.  After the source loop all threads reduce the group
+// sums and evaluate L2P, one target each.
 constexpr int kTileX2 = 512;     // source points per tile of the packed kernel
 
 template <int ND, int TPT>
@@ -583,11 +619,11 @@ __global__ void __launch_bounds__(128) k_p2p_l2p_f32x2(DevGeom G, DevTaskLists L
                                                        const float* __restrict__ loc, double* __restrict__ phi) {
   static_assert(ND >= 1 && ND <= 2, "packed P2P serves one or two densities");
   constexpr int kTile = kTileX2;
-  constexpr int PPT = kTile / 128;
-  __shared__ __align__(16) float sx[2][kTile];
-  __shared__ __align__(16) float sy[2][kTile];
-  __shared__ __align__(16) float sz[2][kTile];
-  __shared__ __align__(16) float sw[2][ND][kTile];
+  constexpr int kPairs = kTile / 2;
+  constexpr int PPT = kPairs / 128;                // pairs loaded per thread per tile
+  __shared__ float4 sxy[2][kPairs];
+  __shared__ float4 szw[2][kPairs];
+  __shared__ float2 sw2[ND > 1 ? 2 : 1][ND > 1 ? kPairs : 1];
   __shared__ int pre[kRunBatch + 1], rst[kRunBatch];
   __shared__ float2 red[ND][128 * TPT];
   const int b = blockIdx.x;
@@ -601,24 +637,20 @@ __global__ void __launch_bounds__(128) k_p2p_l2p_f32x2(DevGeom G, DevTaskLists L
   const int TS = (nt + TPT - 1) / TPT;
   const int NG = 128 / TS;
   const int ts = threadIdx.x % TS, gi_raw = threadIdx.x / TS;
-  const int gi = gi_raw < NG ? gi_raw : NG;
-  float xt[TPT], yt[TPT], zt[TPT];
   float2 X[TPT], Y[TPT], Z[TPT];
-  bool act[TPT];
 #pragma unroll
   for (int u = 0; u < TPT; ++u) {
     const int t = ts + u * TS;
-    act[u] = t < nt;
-    xt[u] = yt[u] = zt[u] = 1e30f;
-    if (act[u]) {
+    float xt = 1e30f, yt = 1e30f, zt = 1e30f;      // padding targets: far away, discarded
+    if (t < nt) {
       const float4 h = G.pthi[tc][tr.x + t], l = G.ptlo[tc][tr.x + t];
-      xt[u] = (h.x - chx) + (l.x - clx);
-      yt[u] = (h.y - chy) + (l.y - cly);
-      zt[u] = (h.z - chz) + (l.z - clz);
+      xt = (h.x - chx) + (l.x - clx);
+      yt = (h.y - chy) + (l.y - cly);
+      zt = (h.z - chz) + (l.z - clz);
     }
-    X[u] = make_float2(xt[u], xt[u]);
-    Y[u] = make_float2(yt[u], yt[u]);
-    Z[u] = make_float2(zt[u], zt[u]);
+    X[u] = make_float2(xt, xt);
+    Y[u] = make_float2(yt, yt);
+    Z[u] = make_float2(zt, zt);
   }
   float shi[TPT][ND], slo[TPT][ND];
 #pragma unroll
@@ -627,8 +659,8 @@ __global__ void __launch_bounds__(128) k_p2p_l2p_f32x2(DevGeom G, DevTaskLists L
     for (int d = 0; d < ND; ++d) shi[u][d] = slo[u][d] = 0.f;
   const int r0 = L.run_off[b], r1 = L.run_off[b + 1];
   const int self_len = L.self_len[b];
-  float4 reg[PPT];
-  float regw[PPT];
+  float4 rxy[PPT], rzw[PPT];
+  float2 rw2[PPT];
   for (int rb = r0; rb < r1; rb += kRunBatch) {
     const int nr = min(kRunBatch, r1 - rb);
     __syncthreads();
@@ -636,31 +668,42 @@ __global__ void __launch_bounds__(128) k_p2p_l2p_f32x2(DevGeom G, DevTaskLists L
     __syncthreads();
     const int total = pre[nr];
     const int ntiles = (total + kTile - 1) / kTile;
+    // source point v of this batch (r: its run), negated, relative to the centre
+    auto fetch = [&](int v, int r, float& x, float& y, float& z, float& w, float& w2) {
+      const int src = rst[r] + (v - pre[r]);
+      const float4 h = G.pthi[sc][src], l = G.ptlo[sc][src];
+      x = -((h.x - chx) + (l.x - clx));
+      y = -((h.y - chy) + (l.y - cly));
+      z = -((h.z - chz) + (l.z - clz));
+      w = W[src];
+      if constexpr (ND > 1) w2 = W[nsp + src];
+    };
     auto load_tile = [&](int t) {
 #pragma unroll
       for (int q = 0; q < PPT; ++q) {
-        const int v = t * kTile + threadIdx.x + q * 128;
-        reg[q] = make_float4(1e30f, 1e30f, 1e30f, 0.f);     // negated padding point
-        regw[q] = 0.f;
-        if (v < total) {
-          const int r = find_run(pre, nr, v);
-          const int src = rst[r] + (v - pre[r]);
-          const float4 h = G.pthi[sc][src], l = G.ptlo[sc][src];
-          reg[q] = make_float4(-((h.x - chx) + (l.x - clx)), -((h.y - chy) + (l.y - cly)),
-                               -((h.z - chz) + (l.z - clz)), W[src]);
-          if (ND > 1) regw[q] = W[nsp + src];
+        const int v0 = t * kTile + 2 * (threadIdx.x + q * 128);
+        float x0 = 1e30f, y0 = 1e30f, z0 = 1e30f, w0 = 0.f, u0 = 0.f;   // negated padding points
+        float x1 = 1e30f, y1 = 1e30f, z1 = 1e30f, w1 = 0.f, u1 = 0.f;
+        if (v0 < total) {
+          int r = find_run(pre, nr, v0);
+          fetch(v0, r, x0, y0, z0, w0, u0);
+          if (v0 + 1 < total) {
+            while (r + 1 < nr && pre[r + 1] <= v0 + 1) ++r;
+            fetch(v0 + 1, r, x1, y1, z1, w1, u1);
+          }
         }
+        rxy[q] = make_float4(x0, x1, y0, y1);
+        rzw[q] = make_float4(z0, z1, w0, w1);
+        rw2[q] = make_float2(u0, u1);
       }
     };
     auto store_tile = [&](int buf) {
 #pragma unroll
       for (int q = 0; q < PPT; ++q) {
-        const int j = threadIdx.x + q * 128;
-        sx[buf][j] = reg[q].x;
-        sy[buf][j] = reg[q].y;
-        sz[buf][j] = reg[q].z;
-        sw[buf][0][j] = reg[q].w;
-        if (ND > 1) sw[buf][ND - 1][j] = regw[q];
+        const int k = threadIdx.x + q * 128;
+        sxy[buf][k] = rxy[q];
+        szw[buf][k] = rzw[q];
+        if constexpr (ND > 1) sw2[buf][k] = rw2[q];
       }
     };
     if (ntiles > 0) {
@@ -673,43 +716,21 @@ __global__ void __launch_bounds__(128) k_p2p_l2p_f32x2(DevGeom G, DevTaskLists L
       if (t + 1 < ntiles) load_tile(t + 1);
       const int m = min(kTile, total - t * kTile);
       const int mp = (m + 1) >> 1;
+      // group gi_raw's contiguous pair range, odd length
+      const int len = ((mp + NG - 1) / NG) | 1;
+      const int k0 = gi_raw < NG ? min(gi_raw * len, mp) : mp;
+      const int k1 = min(k0 + len, mp);
+      // pairs that hold one of the leaf's own points (first run of a VtV list)
+      const int ks = rb == r0 ? max(0, min(mp, (self_len - t * kTile + 1) >> 1)) : 0;
       float2 acc[TPT][ND];
 #pragma unroll
       for (int u = 0; u < TPT; ++u)
 #pragma unroll
         for (int d = 0; d < ND; ++d) acc[u][d] = make_float2(0.f, 0.f);
-      const int kstart = gi_raw < NG ? gi : mp;
-      const float2* px = reinterpret_cast<const float2*>(sx[cur]);
-      const float2* py = reinterpret_cast<const float2*>(sy[cur]);
-      const float2* pz = reinterpret_cast<const float2*>(sz[cur]);
-      if (rb == r0 && t * kTile < self_len) {
-        for (int k = kstart; k < mp; k += NG) {
-          const float2 nx = px[k], ny = py[k], nz = pz[k];
-#pragma unroll
-          for (int u = 0; u < TPT; ++u) {
-            const float2 dx = __fadd2_rn(X[u], nx), dy = __fadd2_rn(Y[u], ny), dz = __fadd2_rn(Z[u], nz);
-            const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
-            const float2 ri = make_float2(r2.x > 0.f ? rsqrt_ftz(r2.x) : 0.f, r2.y > 0.f ? rsqrt_ftz(r2.y) : 0.f);
-#pragma unroll
-            for (int d = 0; d < ND; ++d)
-              acc[u][d] = __ffma2_rn(reinterpret_cast<const float2*>(sw[cur][d])[k], ri, acc[u][d]);
-          }
-        }
-      } else {
-#pragma unroll 4
-        for (int k = kstart; k < mp; k += NG) {
-          const float2 nx = px[k], ny = py[k], nz = pz[k];
-#pragma unroll
-          for (int u = 0; u < TPT; ++u) {
-            const float2 dx = __fadd2_rn(X[u], nx), dy = __fadd2_rn(Y[u], ny), dz = __fadd2_rn(Z[u], nz);
-            const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
-            const float2 ri = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
-#pragma unroll
-            for (int d = 0; d < ND; ++d)
-              acc[u][d] = __ffma2_rn(reinterpret_cast<const float2*>(sw[cur][d])[k], ri, acc[u][d]);
-          }
-        }
-      }
+      const float2* w2 = nullptr;
+      if constexpr (ND > 1) w2 = sw2[cur];
+      if (k0 < ks) p2p_pairs_x2<ND, TPT, true>(sxy[cur], szw[cur], w2, k0, min(k1, ks), X, Y, Z, acc);
+      p2p_pairs_x2<ND, TPT, false>(sxy[cur], szw[cur], w2, max(k0, ks), k1, X, Y, Z, acc);
 #pragma unroll
       for (int u = 0; u < TPT; ++u)
 #pragma unroll
@@ -726,25 +747,24 @@ __global__ void __launch_bounds__(128) k_p2p_l2p_f32x2(DevGeom G, DevTaskLists L
 #pragma unroll
     for (int d = 0; d < ND; ++d) red[d][u * 128 + threadIdx.x] = make_float2(shi[u][d], slo[u][d]);
   __syncthreads();
-  if (gi_raw == 0) {
+  // every thread: one target, the group sums in group order, then L2P
+  const double inv_s = 1.0 / cs.w;
+  for (int tt = threadIdx.x; tt < nt; tt += 128) {
+    const int u = tt / TS, tsl = tt - u * TS;
+    double near[ND];
 #pragma unroll
-    for (int u = 0; u < TPT; ++u) {
-      if (!act[u]) continue;
-      double near[ND];
-#pragma unroll
-      for (int d = 0; d < ND; ++d) {
-        float hi = 0.f, lo = 0.f;
-        for (int g = 0; g < NG; ++g) {
-          const float2 v = red[d][u * 128 + g * TS + ts];
-          two_sum_f(hi, lo, v.x);
-          lo += v.y;
-        }
-        near[d] = (double)hi + (double)lo;
+    for (int d = 0; d < ND; ++d) {
+      float hi = 0.f, lo = 0.f;
+      for (int g = 0; g < NG; ++g) {
+        const float2 v = red[d][u * 128 + g * TS + tsl];
+        two_sum_f(hi, lo, v.x);
+        lo += v.y;
       }
-      const double inv_s = 1.0 / cs.w;
-      l2p_and_store<float, ND>(G, leaf, ndp, loc, xt[u] * inv_s, yt[u] * inv_s, zt[u] * inv_s, near, tr.x + ts + u * TS,
-                               ntp, phi);
+      near[d] = (double)hi + (double)lo;
     }
+    const float4 h = G.pthi[tc][tr.x + tt], l = G.ptlo[tc][tr.x + tt];
+    const float xt = (h.x - chx) + (l.x - clx), yt = (h.y - chy) + (l.y - cly), zt = (h.z - chz) + (l.z - clz);
+    l2p_and_store<float, ND>(G, leaf, ndp, loc, xt * inv_s, yt * inv_s, zt * inv_s, near, tr.x + tt, ntp, phi);
   }
 }
 
