@@ -85,6 +85,7 @@ struct TaskDev {
   int64_t p2p_pairs = 0, near_boxes = 0, m2l_pairs = 0, nnz = 0, tc_entries = 0, tc_rows = 0;
   int64_t m2l_pairs_q[kMaxP + 1] = {};     // box pairs of the interaction phase per expansion order
   double tc_mma_flop = 0;              // executed MMA flops of the tensor-core M2L per density
+  int64_t p2p_src_q[5] = {};           // near-field source points per target leaf: min, median, p90, p99, max
 };
 
 }  // namespace
@@ -226,17 +227,110 @@ static int upload_task(bcfmm_ctx* C, const HostSetup& H, int t) {
   L.n_p2p = (int)T.p2p_leaf.size();
   int *p2p_leaf, *near_off, *near_box, *m2l_tgt, *vl_off, *vl_src, *p2m_leaf, *l2p_leaf;
   uint16_t* vl_code;
-  CU(m.upload(&p2p_leaf, T.p2p_leaf.data(), T.p2p_leaf.size(), st));
-  CU(m.upload(&near_off, T.near_off.data(), T.near_off.size(), st));
-  CU(m.upload(&near_box, T.near_box.data(), T.near_box.size(), st));
-  L.p2p_leaf = p2p_leaf; L.near_off = near_off; L.near_box = near_box;
   {
+    // near-field blocks (one per target leaf) in descending order of work,
+    // source points x (targets + 8): the longest blocks start first and the
+    // launch ends without a tail of a few long leaves
+    const int n = L.n_p2p;
+    std::vector<int> ord(n);
+    std::vector<double> work(n);
+    for (int i = 0; i < n; ++i) {
+      ord[i] = i;
+      int64_t ns = 0;
+      for (int r = T.run_off[i]; r < T.run_off[i + 1]; ++r) ns += T.runs[2 * r + 1] - T.runs[2 * r];
+      const HostBox& B = H.box[T.p2p_leaf[i]];
+      work[i] = (double)ns * (double)(B.pt1[T.tgt_cls] - B.pt0[T.tgt_cls] + 8);
+    }
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return work[a] > work[b]; });
+    std::vector<int> leaf(n), noff(1, 0), nbox, roff(1, 0), runs, self(n);
+    for (int i = 0; i < n; ++i) {
+      const int o = ord[i];
+      leaf[i] = T.p2p_leaf[o];
+      self[i] = T.self_len[o];
+      for (int k = T.near_off[o]; k < T.near_off[o + 1]; ++k) nbox.push_back(T.near_box[k]);
+      noff.push_back((int)nbox.size());
+      for (int r = T.run_off[o]; r < T.run_off[o + 1]; ++r) { runs.push_back(T.runs[2 * r]); runs.push_back(T.runs[2 * r + 1]); }
+      roff.push_back((int)runs.size() / 2);
+    }
+    CU(m.upload(&p2p_leaf, leaf.data(), leaf.size(), st));
+    CU(m.upload(&near_off, noff.data(), noff.size(), st));
+    CU(m.upload(&near_box, nbox.data(), nbox.size(), st));
+    L.p2p_leaf = p2p_leaf; L.near_off = near_off; L.near_box = near_box;
     int *run_off, *self_len;
-    int2* runs;
-    CU(m.upload(&run_off, T.run_off.data(), T.run_off.size(), st));
-    CU(m.upload(&self_len, T.self_len.data(), T.self_len.size(), st));
-    CU(m.upload(&runs, reinterpret_cast<const int2*>(T.runs.data()), T.runs.size() / 2, st));
-    L.run_off = run_off; L.runs = runs; L.self_len = self_len;
+    int2* rd;
+    CU(m.upload(&run_off, roff.data(), roff.size(), st));
+    CU(m.upload(&self_len, self.data(), self.size(), st));
+    CU(m.upload(&rd, reinterpret_cast<const int2*>(runs.data()), runs.size() / 2, st));
+    L.run_off = run_off; L.runs = rd; L.self_len = self_len;
+  }
+  {
+    // blocks of the packed FP32 near field: a leaf whose list holds more
+    // than kChunk source points is cut into near-equal chunks (its runs
+    // split at the chunk boundaries; the leaf's own run, at most 128
+    // points, stays whole in chunk 0), each chunk one block; all blocks in
+    // descending order of work
+    constexpr int64_t kChunk = 8192;
+    struct Blk { int leaf, self, grp, chunk, nt; int64_t ns; std::vector<int> runs; };
+    std::vector<Blk> blk;
+    std::vector<int2> ginfo;
+    int rows = 0;
+    for (size_t i = 0; i < T.p2p_leaf.size(); ++i) {
+      int64_t ns = 0;
+      for (int r = T.run_off[i]; r < T.run_off[i + 1]; ++r) ns += T.runs[2 * r + 1] - T.runs[2 * r];
+      const HostBox& B = H.box[T.p2p_leaf[i]];
+      const int nt = B.pt1[T.tgt_cls] - B.pt0[T.tgt_cls];
+      const int nch = (int)std::max<int64_t>(1, (ns + kChunk - 1) / kChunk);
+      const int64_t per = (ns + nch - 1) / nch;
+      const int g = nch > 1 ? (int)ginfo.size() : -1;
+      if (nch > 1) { ginfo.push_back(make_int2(rows, nch)); rows += nch; }
+      Blk cur{T.p2p_leaf[i], T.self_len[i], g, 0, nt, 0, {}};
+      for (int r = T.run_off[i]; r < T.run_off[i + 1]; ++r) {
+        int s0 = T.runs[2 * r];
+        const int e0 = T.runs[2 * r + 1];
+        while (s0 < e0) {
+          const bool last = cur.chunk + 1 == nch;
+          const int take = last ? e0 - s0 : (int)std::min<int64_t>(e0 - s0, per - cur.ns);
+          cur.runs.push_back(s0);
+          cur.runs.push_back(s0 + take);
+          cur.ns += take;
+          s0 += take;
+          if (!last && cur.ns == per) {
+            const int c = cur.chunk + 1;
+            blk.push_back(std::move(cur));
+            cur = Blk{T.p2p_leaf[i], 0, g, c, nt, 0, {}};
+          }
+        }
+      }
+      blk.push_back(std::move(cur));
+    }
+    std::stable_sort(blk.begin(), blk.end(), [](const Blk& a, const Blk& b) {
+      return (double)a.ns * (a.nt + 8) > (double)b.ns * (b.nt + 8);
+    });
+    std::vector<int> leaf, roff(1, 0), runs, self;
+    std::vector<int2> grp;
+    for (const Blk& k : blk) {
+      leaf.push_back(k.leaf);
+      self.push_back(k.self);
+      grp.push_back(make_int2(k.grp, k.chunk));
+      runs.insert(runs.end(), k.runs.begin(), k.runs.end());
+      roff.push_back((int)runs.size() / 2);
+    }
+    int *sl, *sro, *ss;
+    int2 *srn, *sg, *gi;
+    unsigned* gc;
+    float2* scr;
+    L.sp_n = (int)blk.size();
+    CU(m.upload(&sl, leaf.data(), leaf.size(), st));
+    CU(m.upload(&sro, roff.data(), roff.size(), st));
+    CU(m.upload(&srn, reinterpret_cast<const int2*>(runs.data()), runs.size() / 2, st));
+    CU(m.upload(&ss, self.data(), self.size(), st));
+    CU(m.upload(&sg, grp.data(), grp.size(), st));
+    CU(m.upload(&gi, ginfo.data(), ginfo.size(), st));
+    CU(m.alloc(&gc, ginfo.size()));
+    CU(cudaMemsetAsync(gc, 0, std::max<size_t>(1, ginfo.size()) * sizeof(unsigned), st));
+    CU(m.alloc(&scr, (size_t)rows * 2 * 128));       // up to two densities
+    L.sp_leaf = sl; L.sp_run_off = sro; L.sp_runs = srn; L.sp_self = ss;
+    L.sp_grp = sg; L.grp_info = gi; L.grp_cnt = gc; L.sp_scratch = scr;
   }
   L.n_m2l = (int)T.m2l_tgt.size();
   CU(m.upload(&m2l_tgt, T.m2l_tgt.data(), T.m2l_tgt.size(), st));
@@ -520,6 +614,7 @@ static int upload_task(bcfmm_ctx* C, const HostSetup& H, int t) {
   D.near_boxes = (int64_t)T.near_box.size();
   D.m2l_pairs = (int64_t)T.vl_src.size();
   D.p2p_pairs = 0;
+  std::vector<int64_t> srcs;
   for (size_t i = 0; i < T.p2p_leaf.size(); ++i) {
     const HostBox& B = H.box[T.p2p_leaf[i]];
     int64_t nt = B.pt1[tc] - B.pt0[tc], ns = 0;
@@ -528,6 +623,13 @@ static int upload_task(bcfmm_ctx* C, const HostSetup& H, int t) {
       ns += S.pt1[sc] - S.pt0[sc];
     }
     D.p2p_pairs += nt * ns;
+    srcs.push_back(ns);
+  }
+  if (!srcs.empty()) {
+    std::sort(srcs.begin(), srcs.end());
+    const size_t n = srcs.size();
+    const size_t at[5] = {0, n / 2, (n * 9) / 10, (n * 99) / 100, n - 1};
+    for (int k = 0; k < 5; ++k) D.p2p_src_q[k] = srcs[at[k]];
   }
   return BCFMM_OK;
 }
@@ -1688,6 +1790,8 @@ extern "C" int bcfmm_stats(const bcfmm_ctx* C, char* json, size_t cap) {
     per_q += "], \"m2l_pairs_by_order\": [";
     for (int q = 0; q <= C->prm.p; ++q) per_q += std::to_string(D.m2l_pairs_q[q]) + (q < C->prm.p ? ", " : "");
     per_q += "], \"generic_m2l_targets\": " + std::to_string(C->ty.g ? D.tys.nsimt : (D.tcs.nsimt > 0 ? D.tcs.nsimt : 0));
+    per_q += ", \"p2p_sources_per_leaf\": [";
+    for (int k = 0; k < 5; ++k) per_q += std::to_string(D.p2p_src_q[k]) + (k < 4 ? ", " : "]");
     snprintf(b, sizeof b,
              "\"%s\": {\"p2p_pairs\": %lld, \"near_boxes\": %lld, \"m2l_pairs\": %lld, \"near_pairs\": %lld, "
              "\"p2p_leaves\": %d, \"m2l_targets\": %d, \"p2m_leaves\": %d, \"tc_entries\": %lld, "

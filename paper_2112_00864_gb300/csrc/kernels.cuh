@@ -47,6 +47,20 @@ struct DevTaskLists {
   int tc_ntile;
   const int* tc_tile_tgt;        // [ntile][128]
   int* err;                      // device error word (bounded waits)
+  // the packed FP32 near field's blocks: target leaves whose source lists
+  // exceed one chunk are cut into chunks (runs split at chunk boundaries);
+  // a chunk block writes its per-target sums to its scratch row and the
+  // last chunk of a leaf to finish (ticket counter) adds the rows in chunk
+  // order and evaluates L2P
+  int sp_n;                      // blocks
+  const int* sp_leaf;            // [sp_n] target leaf box
+  const int* sp_run_off;         // [sp_n + 1] into sp_runs
+  const int2* sp_runs;           // source runs (start, end) of the chunks
+  const int* sp_self;            // [sp_n] points of the leaf's own run (chunk 0 of a VtV list), else 0
+  const int2* sp_grp;            // [sp_n] (split leaf index or -1, chunk index)
+  const int2* grp_info;          // [split leaves] (first scratch row, chunks)
+  unsigned* grp_cnt;             // [split leaves] tickets, zero between launches
+  float2* sp_scratch;            // [rows][ND][128] (hi, lo) per target
 };
 
 // launchers (return cudaGetLastError())

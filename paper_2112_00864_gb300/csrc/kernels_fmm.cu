@@ -627,7 +627,7 @@ __global__ void __launch_bounds__(128) k_p2p_l2p_f32x2(DevGeom G, DevTaskLists L
   __shared__ int pre[kRunBatch + 1], rst[kRunBatch];
   __shared__ float2 red[ND][128 * TPT];
   const int b = blockIdx.x;
-  const int leaf = L.p2p_leaf[b];
+  const int leaf = L.sp_leaf[b];
   const int sc = L.src_cls, tc = L.tgt_cls;
   const double4_32a cs = G.box_cs[leaf];
   float chx, clx, chy, cly, chz, clz;
@@ -657,14 +657,14 @@ __global__ void __launch_bounds__(128) k_p2p_l2p_f32x2(DevGeom G, DevTaskLists L
   for (int u = 0; u < TPT; ++u)
 #pragma unroll
     for (int d = 0; d < ND; ++d) shi[u][d] = slo[u][d] = 0.f;
-  const int r0 = L.run_off[b], r1 = L.run_off[b + 1];
-  const int self_len = L.self_len[b];
+  const int r0 = L.sp_run_off[b], r1 = L.sp_run_off[b + 1];
+  const int self_len = L.sp_self[b];
   float4 rxy[PPT], rzw[PPT];
   float2 rw2[PPT];
   for (int rb = r0; rb < r1; rb += kRunBatch) {
     const int nr = min(kRunBatch, r1 - rb);
     __syncthreads();
-    scan_runs(L.runs + rb, nr, pre, rst);
+    scan_runs(L.sp_runs + rb, nr, pre, rst);
     __syncthreads();
     const int total = pre[nr];
     const int ntiles = (total + kTile - 1) / kTile;
@@ -747,7 +747,38 @@ __global__ void __launch_bounds__(128) k_p2p_l2p_f32x2(DevGeom G, DevTaskLists L
 #pragma unroll
     for (int d = 0; d < ND; ++d) red[d][u * 128 + threadIdx.x] = make_float2(shi[u][d], slo[u][d]);
   __syncthreads();
-  // every thread: one target, the group sums in group order, then L2P
+  // every thread: one target, the group sums in group order; a chunk of a
+  // split leaf stores them in its scratch row, and the leaf's last chunk
+  // to finish adds the rows in chunk order; then L2P
+  const int2 grp = L.sp_grp[b];
+  __shared__ int last_chunk;
+  if (grp.x >= 0) {
+    const int2 gi = L.grp_info[grp.x];
+    float2* row = L.sp_scratch + (int64_t)(gi.x + grp.y) * ND * 128;
+    for (int tt = threadIdx.x; tt < nt; tt += 128) {
+      const int u = tt / TS, tsl = tt - u * TS;
+#pragma unroll
+      for (int d = 0; d < ND; ++d) {
+        float hi = 0.f, lo = 0.f;
+        for (int g = 0; g < NG; ++g) {
+          const float2 v = red[d][u * 128 + g * TS + tsl];
+          two_sum_f(hi, lo, v.x);
+          lo += v.y;
+        }
+        __stcg(row + d * 128 + tt, make_float2(hi, lo));
+      }
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const unsigned ticket = atomicAdd(L.grp_cnt + grp.x, 1u);
+      last_chunk = ticket + 1 == (unsigned)gi.y;
+      if (last_chunk) L.grp_cnt[grp.x] = 0u;      // ready for the next launch
+    }
+    __syncthreads();
+    if (!last_chunk) return;
+    __threadfence();
+  }
   const double inv_s = 1.0 / cs.w;
   for (int tt = threadIdx.x; tt < nt; tt += 128) {
     const int u = tt / TS, tsl = tt - u * TS;
@@ -755,10 +786,19 @@ __global__ void __launch_bounds__(128) k_p2p_l2p_f32x2(DevGeom G, DevTaskLists L
 #pragma unroll
     for (int d = 0; d < ND; ++d) {
       float hi = 0.f, lo = 0.f;
-      for (int g = 0; g < NG; ++g) {
-        const float2 v = red[d][u * 128 + g * TS + tsl];
-        two_sum_f(hi, lo, v.x);
-        lo += v.y;
+      if (grp.x < 0) {
+        for (int g = 0; g < NG; ++g) {
+          const float2 v = red[d][u * 128 + g * TS + tsl];
+          two_sum_f(hi, lo, v.x);
+          lo += v.y;
+        }
+      } else {
+        const int2 gi = L.grp_info[grp.x];
+        for (int c = 0; c < gi.y; ++c) {
+          const float2 v = __ldcg(L.sp_scratch + (int64_t)(gi.x + c) * ND * 128 + d * 128 + tt);
+          two_sum_f(hi, lo, v.x);
+          lo += v.y;
+        }
       }
       near[d] = (double)hi + (double)lo;
     }
@@ -859,8 +899,8 @@ cudaError_t launch_p2p_l2p_f32(const DevGeom& G, const DevTaskLists& L, const fl
                                int64_t ntgt_pts, int ndp, const float* loc, double* phi, cudaStream_t st) {
   if (L.n_p2p == 0) return cudaSuccess;
   switch (ndp) {
-    case 1: k_p2p_l2p_f32x2<1, 4><<<L.n_p2p, 128, 0, st>>>(G, L, W, nsrc_pts, ntgt_pts, ndp, loc, phi); break;
-    case 2: k_p2p_l2p_f32x2<2, 2><<<L.n_p2p, 128, 0, st>>>(G, L, W, nsrc_pts, ntgt_pts, ndp, loc, phi); break;
+    case 1: k_p2p_l2p_f32x2<1, 4><<<L.sp_n, 128, 0, st>>>(G, L, W, nsrc_pts, ntgt_pts, ndp, loc, phi); break;
+    case 2: k_p2p_l2p_f32x2<2, 2><<<L.sp_n, 128, 0, st>>>(G, L, W, nsrc_pts, ntgt_pts, ndp, loc, phi); break;
     case 4: k_p2p_l2p_f32<4><<<L.n_p2p, 128, 0, st>>>(G, L, W, nsrc_pts, ntgt_pts, ndp, loc, phi); break;
     case 8: k_p2p_l2p_f32<8><<<L.n_p2p, 128, 0, st>>>(G, L, W, nsrc_pts, ntgt_pts, ndp, loc, phi); break;
     case 16: k_p2p_l2p_f32<16><<<L.n_p2p, 128, 0, st>>>(G, L, W, nsrc_pts, ntgt_pts, ndp, loc, phi); break;
