@@ -37,14 +37,17 @@ cudaError_t launch_weights(const DevGeom& G, int cls, int64_t n, const double* d
 
 // ---------------------------------------------------------------- P2M
 // One CTA per leaf; thread per coefficient; powers of the scaled offsets
-// staged in shared memory for a chunk of 64 points.
+// staged in shared memory for a chunk of 64 points, rows of kPwS = 65
+// (threads of one warp read rows of different exponents at the same point:
+// an odd stride puts them in different banks).
+constexpr int kPwS = 65;
 template <typename T>
 __global__ void k_p2m(DevGeom G, const int* __restrict__ leaves, int cls, const T* __restrict__ W, int64_t nsp,
                       int ndp, T* __restrict__ mom) {
   extern __shared__ unsigned char smraw[];
   const int P = G.p, np = G.np;
   T* pw = reinterpret_cast<T*>(smraw);               // [3][P+1][64]
-  T* ws = pw + 3 * (P + 1) * 64;                     // [ndp][64]
+  T* ws = pw + 3 * (P + 1) * kPwS;                   // [ndp][64]
   const int leaf = leaves[blockIdx.x];
   const double4_32a cs = G.box_cs[leaf];
   const int2 r = G.box_rng[cls][leaf];
@@ -57,7 +60,7 @@ __global__ void k_p2m(DevGeom G, const int* __restrict__ leaves, int cls, const 
       const T d[3] = {(T)((y.x - cs.x) * inv_s), (T)((y.y - cs.y) * inv_s), (T)((y.z - cs.z) * inv_s)};
       for (int ax = 0; ax < 3; ++ax) {
         T v = (T)1;
-        for (int k = 0; k <= P; ++k) { pw[(ax * (P + 1) + k) * 64 + j] = v; v *= d[ax]; }
+        for (int k = 0; k <= P; ++k) { pw[(ax * (P + 1) + k) * kPwS + j] = v; v *= d[ax]; }
       }
       for (int dd = 0; dd < ndp; ++dd) ws[dd * 64 + j] = W[(int64_t)dd * nsp + j0 + j];
     }
@@ -65,9 +68,9 @@ __global__ void k_p2m(DevGeom G, const int* __restrict__ leaves, int cls, const 
     for (int q = threadIdx.x; q < np; q += blockDim.x) {
       const int mi = G.mi[q];
       const int a = mi & 255, b = (mi >> 8) & 255, c = (mi >> 16) & 255;
-      const T* px = pw + (0 * (P + 1) + a) * 64;
-      const T* py = pw + (1 * (P + 1) + b) * 64;
-      const T* pz = pw + (2 * (P + 1) + c) * 64;
+      const T* px = pw + (0 * (P + 1) + a) * kPwS;
+      const T* py = pw + (1 * (P + 1) + b) * kPwS;
+      const T* pz = pw + (2 * (P + 1) + c) * kPwS;
       for (int dd = 0; dd < ndp; ++dd) {
         T acc = 0;
         for (int j = 0; j < m; ++j) acc += ws[dd * 64 + j] * px[j] * py[j] * pz[j];
@@ -81,7 +84,7 @@ template <typename T>
 cudaError_t launch_p2m(const DevGeom& G, const DevTaskLists& L, const T* W, int64_t nsrc_pts, int ndp,
                        T* mom, cudaStream_t st) {
   if (L.n_p2m == 0) return cudaSuccess;
-  size_t sm = sizeof(T) * (3 * (G.p + 1) * 64 + ndp * 64);
+  size_t sm = sizeof(T) * (3 * (G.p + 1) * kPwS + ndp * 64);
   k_p2m<T><<<L.n_p2m, 128, sm, st>>>(G, L.p2m_leaf, L.src_cls, W, nsrc_pts, ndp, mom);
   return cudaGetLastError();
 }
@@ -934,6 +937,7 @@ __global__ void k_elem_sum(DevGeom G, DevTaskLists L, const double* __restrict__
       s = G.pt64[tc][pos].w * phi[(int64_t)d * ntp + pos];
     }
     const int64_t k0 = L.cor_off[e], k1 = L.cor_off[e + 1];
+#pragma unroll 4
     for (int64_t k = k0 + lane; k < k1; k += 32) s += L.cor_val[k] * dens[(int64_t)d * L.nsrc_el + L.cor_col[k]];
     // BtV double layer: - (N - Q) of dG/dn_y times g
     if (dens_dl)
@@ -965,7 +969,7 @@ __global__ void k_p2m_dl(DevGeom G, const int* __restrict__ leaves, const T* __r
   extern __shared__ unsigned char smraw[];
   const int P = G.p, np = G.np;
   T* pw = reinterpret_cast<T*>(smraw);               // [3][P+1][64]
-  T* wn = pw + 3 * (P + 1) * 64;                     // [ndp][3][64]: Wg n_i / s
+  T* wn = pw + 3 * (P + 1) * kPwS;                   // [ndp][3][64]: Wg n_i / s
   const int leaf = leaves[blockIdx.x];
   const double4_32a cs = G.box_cs[leaf];
   const int2 r = G.box_rng[1][leaf];
@@ -978,7 +982,7 @@ __global__ void k_p2m_dl(DevGeom G, const int* __restrict__ leaves, const T* __r
       const T d[3] = {(T)((y.x - cs.x) * inv_s), (T)((y.y - cs.y) * inv_s), (T)((y.z - cs.z) * inv_s)};
       for (int ax = 0; ax < 3; ++ax) {
         T v = (T)1;
-        for (int k = 0; k <= P; ++k) { pw[(ax * (P + 1) + k) * 64 + j] = v; v *= d[ax]; }
+        for (int k = 0; k <= P; ++k) { pw[(ax * (P + 1) + k) * kPwS + j] = v; v *= d[ax]; }
       }
       const double4_32a nr = G.tri_nrm[G.pt_elem[1][j0 + j]];
       for (int dd = 0; dd < ndp; ++dd) {
@@ -992,9 +996,9 @@ __global__ void k_p2m_dl(DevGeom G, const int* __restrict__ leaves, const T* __r
     for (int q = threadIdx.x; q < np; q += blockDim.x) {
       const int mi = G.mi[q];
       const int a = mi & 255, b = (mi >> 8) & 255, c = (mi >> 16) & 255;
-      const T* px = pw + (0 * (P + 1)) * 64;
-      const T* py = pw + (1 * (P + 1)) * 64;
-      const T* pz = pw + (2 * (P + 1)) * 64;
+      const T* px = pw + (0 * (P + 1)) * kPwS;
+      const T* py = pw + (1 * (P + 1)) * kPwS;
+      const T* pz = pw + (2 * (P + 1)) * kPwS;
       for (int dd = 0; dd < ndp; ++dd) {
         const T* wx = wn + (dd * 3 + 0) * 64;
         const T* wy = wn + (dd * 3 + 1) * 64;
@@ -1002,9 +1006,9 @@ __global__ void k_p2m_dl(DevGeom G, const int* __restrict__ leaves, const T* __r
         T acc = 0;
         for (int j = 0; j < m; ++j) {
           T g = 0;
-          if (a) g += (T)a * wx[j] * px[(a - 1) * 64 + j] * py[b * 64 + j] * pz[c * 64 + j];
-          if (b) g += (T)b * wy[j] * px[a * 64 + j] * py[(b - 1) * 64 + j] * pz[c * 64 + j];
-          if (c) g += (T)c * wz[j] * px[a * 64 + j] * py[b * 64 + j] * pz[(c - 1) * 64 + j];
+          if (a) g += (T)a * wx[j] * px[(a - 1) * kPwS + j] * py[b * kPwS + j] * pz[c * kPwS + j];
+          if (b) g += (T)b * wy[j] * px[a * kPwS + j] * py[(b - 1) * kPwS + j] * pz[c * kPwS + j];
+          if (c) g += (T)c * wz[j] * px[a * kPwS + j] * py[b * kPwS + j] * pz[(c - 1) * kPwS + j];
           acc += g;
         }
         mom[((int64_t)leaf * ndp + dd) * G.ms + q] -= acc;
@@ -1017,7 +1021,7 @@ template <typename T>
 cudaError_t launch_p2m_dl(const DevGeom& G, const DevTaskLists& L, const T* W, int64_t nsrc_pts, int ndp, T* mom,
                           cudaStream_t st) {
   if (L.n_p2m == 0) return cudaSuccess;
-  const size_t sm = sizeof(T) * (3 * (G.p + 1) * 64 + 3 * ndp * 64);
+  const size_t sm = sizeof(T) * (3 * (G.p + 1) * kPwS + 3 * ndp * 64);
   k_p2m_dl<T><<<L.n_p2m, 128, sm, st>>>(G, L.p2m_leaf, W, nsrc_pts, ndp, mom);
   return cudaGetLastError();
 }
