@@ -463,7 +463,12 @@ int bcfmm_debug_near_pairs(const double* verts, int64_t nvert, const int32_t* te
  * schedule built for 1, 7 and 152 SMs (a list entry of a target of order
  * 1..7 missing, duplicated, invented or in a lane whose chunk is another
  * target's; a chunk not in exactly one lane; a target of another order not
- * exactly once in the generic kernel's list).  out: host int64 [12].
+ * exactly once in the generic kernel's list); out[12..14], per task, the
+ * faults of the packed FP32 near field's blocks built with chunks of 96
+ * points and of the library's 8192 (a source point of a leaf's list in no
+ * chunk or in two, a chunk over its size, the leaf's own run not whole at
+ * the front of chunk 0, scratch rows not one per chunk, work increasing
+ * along the block order).  out: host int64 [15].
  * Errors: BCFMM_ERR_ARG, BCFMM_ERR_MESH.
  */
 int bcfmm_debug_list_coverage(const double* verts, const int64_t* vert_off, const int32_t* tets,

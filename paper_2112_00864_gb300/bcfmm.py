@@ -433,7 +433,8 @@ def debug_list_coverage(meshes, **kw) -> np.ndarray:
     batch: [0:3] per task the (target leaf, source point) pairs not covered
     exactly once, [3:6] per task the interaction entries the tensor-core
     tiles get wrong, [6:9] per task the faults of the tensor-core schedule,
-    [9:12] per task the faults of the Taylor-form M2L schedule (see
+    [9:12] per task the faults of the Taylor-form M2L schedule, [12:15] per
+    task the faults of the packed near field's chunk blocks (see
     include/bcfmm.h)."""
     vo, to, ro = [0], [0], [0]
     for m in meshes:
@@ -445,7 +446,7 @@ def debug_list_coverage(meshes, **kw) -> np.ndarray:
     tris = np.ascontiguousarray(np.concatenate([np.asarray(m.tris).reshape(-1, 3) for m in meshes]), np.int32)
     vo, to, ro = (np.asarray(x, np.int64) for x in (vo, to, ro))
     prm = default_params(**kw)
-    out = np.zeros(12, np.int64)
+    out = np.zeros(15, np.int64)
     _check(load().bcfmm_debug_list_coverage(verts.ctypes.data, vo.ctypes.data, tets.ctypes.data, to.ctypes.data,
                                             tris.ctypes.data, ro.ctypes.data, len(meshes), C.byref(prm),
                                             out.ctypes.data))

@@ -264,71 +264,26 @@ static int upload_task(bcfmm_ctx* C, const HostSetup& H, int t) {
     L.run_off = run_off; L.runs = rd; L.self_len = self_len;
   }
   {
-    // blocks of the packed FP32 near field: a leaf whose list holds more
-    // than kChunk source points is cut into near-equal chunks (its runs
-    // split at the chunk boundaries; the leaf's own run, at most 128
-    // points, stays whole in chunk 0), each chunk one block; all blocks in
-    // descending order of work
-    constexpr int64_t kChunk = 8192;
-    struct Blk { int leaf, self, grp, chunk, nt; int64_t ns; std::vector<int> runs; };
-    std::vector<Blk> blk;
-    std::vector<int2> ginfo;
-    int rows = 0;
-    for (size_t i = 0; i < T.p2p_leaf.size(); ++i) {
-      int64_t ns = 0;
-      for (int r = T.run_off[i]; r < T.run_off[i + 1]; ++r) ns += T.runs[2 * r + 1] - T.runs[2 * r];
-      const HostBox& B = H.box[T.p2p_leaf[i]];
-      const int nt = B.pt1[T.tgt_cls] - B.pt0[T.tgt_cls];
-      const int nch = (int)std::max<int64_t>(1, (ns + kChunk - 1) / kChunk);
-      const int64_t per = (ns + nch - 1) / nch;
-      const int g = nch > 1 ? (int)ginfo.size() : -1;
-      if (nch > 1) { ginfo.push_back(make_int2(rows, nch)); rows += nch; }
-      Blk cur{T.p2p_leaf[i], T.self_len[i], g, 0, nt, 0, {}};
-      for (int r = T.run_off[i]; r < T.run_off[i + 1]; ++r) {
-        int s0 = T.runs[2 * r];
-        const int e0 = T.runs[2 * r + 1];
-        while (s0 < e0) {
-          const bool last = cur.chunk + 1 == nch;
-          const int take = last ? e0 - s0 : (int)std::min<int64_t>(e0 - s0, per - cur.ns);
-          cur.runs.push_back(s0);
-          cur.runs.push_back(s0 + take);
-          cur.ns += take;
-          s0 += take;
-          if (!last && cur.ns == per) {
-            const int c = cur.chunk + 1;
-            blk.push_back(std::move(cur));
-            cur = Blk{T.p2p_leaf[i], 0, g, c, nt, 0, {}};
-          }
-        }
-      }
-      blk.push_back(std::move(cur));
-    }
-    std::stable_sort(blk.begin(), blk.end(), [](const Blk& a, const Blk& b) {
-      return (double)a.ns * (a.nt + 8) > (double)b.ns * (b.nt + 8);
-    });
-    std::vector<int> leaf, roff(1, 0), runs, self;
-    std::vector<int2> grp;
-    for (const Blk& k : blk) {
-      leaf.push_back(k.leaf);
-      self.push_back(k.self);
-      grp.push_back(make_int2(k.grp, k.chunk));
-      runs.insert(runs.end(), k.runs.begin(), k.runs.end());
-      roff.push_back((int)runs.size() / 2);
-    }
+    // blocks of the packed FP32 near field (long leaves cut into chunks)
+    P2pChunks K;
+    build_p2p_chunks(H, t, kP2pChunk, K);
+    std::vector<int2> grp(K.grp.size()), ginfo(K.grp_row.size());
+    for (size_t b = 0; b < K.grp.size(); ++b) grp[b] = make_int2(K.grp[b], K.chunk[b]);
+    for (size_t g = 0; g < K.grp_row.size(); ++g) ginfo[g] = make_int2(K.grp_row[g], K.grp_n[g]);
     int *sl, *sro, *ss;
     int2 *srn, *sg, *gi;
     unsigned* gc;
     float2* scr;
-    L.sp_n = (int)blk.size();
-    CU(m.upload(&sl, leaf.data(), leaf.size(), st));
-    CU(m.upload(&sro, roff.data(), roff.size(), st));
-    CU(m.upload(&srn, reinterpret_cast<const int2*>(runs.data()), runs.size() / 2, st));
-    CU(m.upload(&ss, self.data(), self.size(), st));
+    L.sp_n = (int)K.leaf.size();
+    CU(m.upload(&sl, K.leaf.data(), K.leaf.size(), st));
+    CU(m.upload(&sro, K.run_off.data(), K.run_off.size(), st));
+    CU(m.upload(&srn, reinterpret_cast<const int2*>(K.runs.data()), K.runs.size() / 2, st));
+    CU(m.upload(&ss, K.self.data(), K.self.size(), st));
     CU(m.upload(&sg, grp.data(), grp.size(), st));
     CU(m.upload(&gi, ginfo.data(), ginfo.size(), st));
     CU(m.alloc(&gc, ginfo.size()));
     CU(cudaMemsetAsync(gc, 0, std::max<size_t>(1, ginfo.size()) * sizeof(unsigned), st));
-    CU(m.alloc(&scr, (size_t)rows * 2 * 128));       // up to two densities
+    CU(m.alloc(&scr, (size_t)K.rows * 2 * 128));     // up to two densities
     L.sp_leaf = sl; L.sp_run_off = sro; L.sp_runs = srn; L.sp_self = ss;
     L.sp_grp = sg; L.grp_info = gi; L.grp_cnt = gc; L.sp_scratch = scr;
   }
@@ -1277,6 +1232,75 @@ extern "C" int bcfmm_debug_list_coverage(const double* verts, const int64_t* ver
         }
       }
       out[9 + t] = ybad;
+    }
+    // the packed near field's chunk blocks, cut at a small chunk size (so
+    // that small meshes split) and at the library's: every source point of a
+    // leaf's list in exactly one of its chunks, none other, a chunk within
+    // the size, the leaf's own run whole at the front of chunk 0, split
+    // leaves with chunks 0..n-1 on disjoint scratch rows, work non-increasing
+    for (int t = 0; t < 3; ++t) {
+      const HostTask& T = H.task[t];
+      int64_t kbad = 0;
+      std::vector<int> idx_of(H.box.size(), -1);
+      for (size_t i = 0; i < T.p2p_leaf.size(); ++i) idx_of[T.p2p_leaf[i]] = (int)i;
+      for (int64_t chunk : {(int64_t)96, kP2pChunk}) {
+        P2pChunks K;
+        build_p2p_chunks(H, t, chunk, K);
+        const size_t nb = K.leaf.size();
+        std::vector<std::vector<int>> blocks_of(T.p2p_leaf.size());
+        for (size_t b = 0; b < nb; ++b) {
+          const int i = idx_of[K.leaf[b]];
+          if (i < 0) { ++kbad; continue; }
+          blocks_of[i].push_back((int)b);
+        }
+        std::vector<int> rowuse(K.rows, 0);
+        double prev = 1e300;
+        for (size_t b = 0; b < nb; ++b) {
+          int64_t ns = 0;
+          for (int r = K.run_off[b]; r < K.run_off[b + 1]; ++r) ns += K.runs[2 * r + 1] - K.runs[2 * r];
+          const HostBox& B = H.box[K.leaf[b]];
+          const double w = (double)ns * (B.pt1[T.tgt_cls] - B.pt0[T.tgt_cls] + 8);
+          if (w > prev) ++kbad;
+          prev = w;
+          if (K.grp[b] >= 0 && ns > std::max<int64_t>(chunk, K.self[b])) ++kbad;
+        }
+        for (size_t i = 0; i < T.p2p_leaf.size(); ++i) {
+          std::vector<std::pair<int, int>> want, got;
+          for (int r = T.run_off[i]; r < T.run_off[i + 1]; ++r) want.push_back({T.runs[2 * r], T.runs[2 * r + 1]});
+          const std::vector<int>& bl = blocks_of[i];
+          const int g = bl.empty() ? -2 : K.grp[bl[0]];
+          if (bl.empty() || (g < 0 && bl.size() != 1)) { ++kbad; continue; }
+          std::vector<int> seen(bl.size(), 0);
+          for (int b : bl) {
+            if (K.grp[b] != g) { ++kbad; continue; }
+            const int c = g < 0 ? 0 : K.chunk[b];
+            if (c < 0 || c >= (int)bl.size() || seen[c]++) { ++kbad; continue; }
+            if (g >= 0) {
+              if (K.grp_n[g] != (int)bl.size() || K.grp_row[g] + c >= K.rows) ++kbad;
+              else rowuse[K.grp_row[g] + c]++;
+            }
+            // the leaf's own run: whole, first, in chunk 0 only
+            if (c == 0) {
+              if (K.self[b] != T.self_len[i]) ++kbad;
+              if (T.self_len[i] > 0 && (K.run_off[b] == K.run_off[b + 1] || K.runs[2 * K.run_off[b]] != T.runs[2 * T.run_off[i]] ||
+                                        K.runs[2 * K.run_off[b] + 1] - K.runs[2 * K.run_off[b]] != T.self_len[i]))
+                ++kbad;
+            } else if (K.self[b] != 0) {
+              ++kbad;
+            }
+            for (int r = K.run_off[b]; r < K.run_off[b + 1]; ++r) got.push_back({K.runs[2 * r], K.runs[2 * r + 1]});
+          }
+          // the same points: expand both run lists to point counts
+          std::vector<int> cw, cg;
+          for (auto& pr : want) for (int q = pr.first; q < pr.second; ++q) cw.push_back(q);
+          for (auto& pr : got) for (int q = pr.first; q < pr.second; ++q) cg.push_back(q);
+          std::sort(cw.begin(), cw.end());
+          std::sort(cg.begin(), cg.end());
+          if (cw != cg) kbad += (int64_t)std::max(cw.size(), cg.size());
+        }
+        for (int r = 0; r < K.rows; ++r) kbad += rowuse[r] != 1;
+      }
+      out[12 + t] = kbad;
     }
   } catch (const std::exception& ex) {
     return fail(BCFMM_ERR_ARG, std::string("debug_list_coverage: ") + ex.what());

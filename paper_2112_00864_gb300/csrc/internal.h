@@ -90,6 +90,20 @@ void find_near_pairs(HostSetup& H, double eta_ns);
 // meshes, so the result evaluates every mesh on its own.
 void merge_setups(std::vector<HostSetup>& parts, HostSetup& H);
 
+// Blocks of the packed FP32 near field for one task: a target leaf whose
+// near list holds more than `chunk` source points is cut into near-equal
+// chunks (runs split at the chunk boundaries; the leaf's own run, at most
+// 128 points, stays whole at the front of chunk 0), one block per chunk;
+// blocks in descending order of work, source points x (targets + 8).
+struct P2pChunks {
+  std::vector<int> leaf, run_off, runs, self;   // per block; runs as (start, end) pairs
+  std::vector<int> grp, chunk;                  // split leaf index (-1: whole leaf), chunk index
+  std::vector<int> grp_row, grp_n;              // per split leaf: first scratch row, chunks
+  int rows = 0;                                 // scratch rows (chunks of split leaves)
+};
+constexpr int64_t kP2pChunk = 8192;
+void build_p2p_chunks(const HostSetup& H, int task, int64_t chunk, P2pChunks& out);
+
 // Gauss-Legendre nodes/weights on [0,1] (Newton iteration on P_n).
 void gauss_legendre01(int n, std::vector<double>& x, std::vector<double>& w);
 

@@ -511,6 +511,59 @@ void find_near_pairs(HostSetup& H, double eta_ns) {
 }
 
 // ---------------------------------------------------------------- batches
+void build_p2p_chunks(const HostSetup& H, int t, int64_t chunk, P2pChunks& out) {
+  const HostTask& T = H.task[t];
+  struct Blk { int leaf, self, grp, chunk, nt; int64_t ns; std::vector<int> runs; };
+  std::vector<Blk> blk;
+  out = P2pChunks();
+  for (size_t i = 0; i < T.p2p_leaf.size(); ++i) {
+    int64_t ns = 0;
+    for (int r = T.run_off[i]; r < T.run_off[i + 1]; ++r) ns += T.runs[2 * r + 1] - T.runs[2 * r];
+    const HostBox& B = H.box[T.p2p_leaf[i]];
+    const int nt = B.pt1[T.tgt_cls] - B.pt0[T.tgt_cls];
+    const int nch = (int)std::max<int64_t>(1, (ns + chunk - 1) / chunk);
+    const int64_t per = (ns + nch - 1) / nch;
+    const int g = nch > 1 ? (int)out.grp_row.size() : -1;
+    if (nch > 1) {
+      out.grp_row.push_back(out.rows);
+      out.grp_n.push_back(nch);
+      out.rows += nch;
+    }
+    Blk cur{T.p2p_leaf[i], T.self_len[i], g, 0, nt, 0, {}};
+    for (int r = T.run_off[i]; r < T.run_off[i + 1]; ++r) {
+      int s0 = T.runs[2 * r];
+      const int e0 = T.runs[2 * r + 1];
+      while (s0 < e0) {
+        // the leaf's own run (first in a VtV list) is never cut
+        const bool whole = cur.chunk + 1 == nch || (r == T.run_off[i] && T.self_len[i] > 0);
+        const int take = whole ? e0 - s0 : (int)std::min<int64_t>(e0 - s0, per - cur.ns);
+        cur.runs.push_back(s0);
+        cur.runs.push_back(s0 + take);
+        cur.ns += take;
+        s0 += take;
+        if (cur.chunk + 1 < nch && cur.ns >= per) {
+          const int c = cur.chunk + 1;
+          blk.push_back(std::move(cur));
+          cur = Blk{T.p2p_leaf[i], 0, g, c, nt, 0, {}};
+        }
+      }
+    }
+    blk.push_back(std::move(cur));
+  }
+  std::stable_sort(blk.begin(), blk.end(), [](const Blk& a, const Blk& b) {
+    return (double)a.ns * (a.nt + 8) > (double)b.ns * (b.nt + 8);
+  });
+  out.run_off.push_back(0);
+  for (const Blk& k : blk) {
+    out.leaf.push_back(k.leaf);
+    out.self.push_back(k.self);
+    out.grp.push_back(k.grp);
+    out.chunk.push_back(k.chunk);
+    out.runs.insert(out.runs.end(), k.runs.begin(), k.runs.end());
+    out.run_off.push_back((int)out.runs.size() / 2);
+  }
+}
+
 void merge_setups(std::vector<HostSetup>& P, HostSetup& H) {
   const int nm = (int)P.size();
   H = HostSetup();

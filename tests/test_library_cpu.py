@@ -170,10 +170,11 @@ def test_interactions_covered_exactly_once(lib, leaf_size, eta0, p_level, tc_uni
     from paper_2112_00864_gb300.inputs import ball_bc_mesh, batch_meshes, cube_bc_mesh
     kw = dict(leaf_size=leaf_size, eta0=eta0, p=max(p_level or [7]), tc_unit=tc_unit, p_level=p_level)
     # [0:3] covering of every task, [3:6] the tiles against the lists, [6:9] the
-    # tensor-core schedule, [9:12] the Taylor-form schedule
-    assert list(bcfmm.debug_list_coverage([cube_bc_mesh(0.25, 0.125)], **kw)) == [0] * 12
-    assert list(bcfmm.debug_list_coverage([ball_bc_mesh(2, radial=0.35)], **kw)) == [0] * 12
-    assert list(bcfmm.debug_list_coverage(batch_meshes(4, seed=3, hs=(1 / 4, 1 / 8)), **kw)) == [0] * 12
+    # tensor-core schedule, [9:12] the Taylor-form schedule, [12:15] the packed
+    # near field's chunk blocks (cut at 96 points and at the library's size)
+    assert list(bcfmm.debug_list_coverage([cube_bc_mesh(0.25, 0.125)], **kw)) == [0] * 15
+    assert list(bcfmm.debug_list_coverage([ball_bc_mesh(2, radial=0.35)], **kw)) == [0] * 15
+    assert list(bcfmm.debug_list_coverage(batch_meshes(4, seed=3, hs=(1 / 4, 1 / 8)), **kw)) == [0] * 15
 
 
 def test_near_pairs_equal_brute_force(lib):
