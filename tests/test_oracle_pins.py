@@ -455,3 +455,75 @@ def test_green_representation_poisson():
             ref = _cell_avg(m, uP, tg)
             err.append(np.linalg.norm(num - ref) / np.linalg.norm(ref))
         assert err[0] > 1.8 * err[1] > 1.8 ** 2 * err[2], err
+
+
+def _cube_frame():
+    """Sec. 5's functions on the cube meshes of [0,1]^3 through x' = 2(x - 1/2)."""
+    c = np.array([0.5, 0.5, 0.5])
+    xp = lambda x: 2.0 * (x - c)
+    x0 = np.array([3.0, 0.0, 0.0])
+    uL = lambda x: 1.0 / np.linalg.norm(xp(x) - x0, axis=-1)
+    duL = lambda x, n: -2.0 * np.sum((xp(x) - x0) * n, -1) / np.linalg.norm(xp(x) - x0, axis=-1) ** 3
+    uP = lambda x: np.exp(-np.sum(xp(x) ** 2, -1))
+    fP = lambda x: 4.0 * (6.0 - 4.0 * np.sum(xp(x) ** 2, -1)) * uP(x)
+    duP = lambda x, n: -4.0 * np.sum(xp(x) * n, -1) * uP(x)
+    return uL, duL, uP, fP, duP
+
+
+def _boundary_tets(m):
+    """Tets with a face on the cube's surface (the set B_L of Sec. 2)."""
+    tv = m.verts[m.tets]
+    onb = (np.abs(tv) < 1e-12) | (np.abs(tv - 1.0) < 1e-12)
+    return np.where((onb.sum(1) >= 3).any(1))[0]
+
+
+def test_green_laplace_boundary_tets_need_the_wider_near_rule():
+    """Sec. 5's BtV test on the cube's boundary tets.  With only the
+    touching element pairs on the near rule, the 4 x 3-point product rule on
+    the next ring of triangles keeps a relative error that a self-similar
+    mesh does not shrink: here the error still halves from h = 1/16 to 1/32
+    (4.4e-4 to 2.2e-4 on these 120 targets), and the library's runs at 1/64
+    and 1/128 stay near 1.9e-4.  With eta_ns = 0.5 (that ring on the near rule
+    too) it falls faster than O(h) over the same meshes (8.1e-4, 3.7e-4,
+    1.3e-4) and ends 0.57x below the default at 1/32.  The floor is the
+    product rule's, not the FMM's, the P0 data's or the near rule order's
+    (6 instead of 3 Gauss points changes the error in the third digit)."""
+    uL, duL, _, _, _ = _cube_frame()
+    err = {O.ETA_NS: [], 0.5: []}
+    for inv_h in (8, 16, 32):
+        m = cube_bc_mesh(1 / inv_h, 1 / inv_h)
+        g, q = _p0_boundary_data(m, uL, duL)
+        tg = np.sort(np.random.default_rng(0).choice(_boundary_tets(m), 120, replace=False))
+        vol = O.element_volumes(m)[tg]
+        ref = _cell_avg(m, uL, tg)
+        for en in err:
+            num = (O.direct("btv", m, q[None], targets=tg, eta_ns=en)[0]
+                   - O.direct("btv_dl", m, g[None], targets=tg, eta_ns=en)[0]) / vol
+            err[en].append(np.linalg.norm(num - ref) / np.linalg.norm(ref))
+    wide, default = err[0.5], err[O.ETA_NS]
+    assert wide[0] > 1.8 * wide[1] > 1.8 ** 2 * wide[2], wide
+    # the wider rule converges faster and ends well below the default
+    assert default[1] / default[2] < 0.8 * wide[1] / wide[2], (default, wide)
+    assert wide[2] < 0.7 * default[2], (default, wide)
+
+
+def test_green_poisson_floor_is_the_coarse_interior():
+    """Sec. 5's VtV + BtV test on the cube at h = 1/32: the P0 cell averages
+    of f on the BC mesh's coarse interior cells (a cell is split while larger
+    than half its distance to the surface) fix an error in N~f at every
+    target, the boundary tets included.  Grading the interior twice as
+    finely lowers it at the same h: the floor lies in the interior cells,
+    which Sec. 5 treats with the degree schedule p_l = L - l."""
+    _, _, uP, fP, duP = _cube_frame()
+    err = {}
+    for grade in (0.5, 0.25):
+        m = cube_bc_mesh(1 / 32, 1 / 32, grade=grade)
+        g, q = _p0_boundary_data(m, uP, duP)
+        f = _cell_avg(m, fP, np.arange(m.ntet))
+        tg = np.sort(np.random.default_rng(0).choice(_boundary_tets(m), 120, replace=False))
+        vol = O.element_volumes(m)[tg]
+        num = (O.direct("btv", m, q[None], targets=tg)[0] - O.direct("btv_dl", m, g[None], targets=tg)[0]
+               + O.direct("vtv", m, f[None], targets=tg)[0]) / vol
+        ref = _cell_avg(m, uP, tg)
+        err[grade] = np.linalg.norm(num - ref) / np.linalg.norm(ref)
+    assert err[0.25] < 0.6 * err[0.5], err
