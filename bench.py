@@ -59,7 +59,7 @@ def workload():
 # order schedule q_l = min(7, q0 + L - l) (Sec. 4.3, Eq. def:q0).  Sec. 5
 # runs eta0 = 0.5 with q0 = 4; measured on this GPU, eta0 = 0.6 (93 instead
 # of 171 near-field boxes: 44% fewer P2P pairs) with q0 = 6 holds the error
-# at 2.4e-7 on this mesh (<= 5e-7 on the test meshes) in 25% less time than
+# at 1.9e-7 on this mesh (<= 5e-7 on the test meshes) in 25% less time than
 # eta0 = 0.5 with q0 = 5, and eta0 = 0.65 (81 boxes) leaves too little margin
 CHOSEN = dict(p=7, q0=6, eta0=0.6, leaf_size=128, precision="fp32")
 PLAIN = dict(p=7, q0=6, eta0=0.6, leaf_size=128, precision="fp64")
