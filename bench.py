@@ -88,6 +88,23 @@ def peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def spmv_roofline(st: dict, sums_ms: float, ndens: int, pk: dict) -> dict:
+    """Roofline of the near-correction SpMV inside the element sums
+    (k_elem_sum, VtV + VtB): algorithmic bytes 12 per near pair (int32
+    column + FP64 correction) plus 8 per near pair and density (the gathered
+    density), over the stage's device time, against the measured copy
+    bandwidth.  The per-element sums of the point potentials ride along
+    uncounted."""
+    nnz = sum(int(st.get(t, {}).get("near_pairs", 0)) for t in ("vtv", "vtb"))
+    byts = nnz * (12 + 8 * ndens)
+    ach = byts / (sums_ms * 1e-3) / 1e9 if sums_ms > 0 else None
+    return {"kernel": "k_elem_sum", "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": ach / pk["hbm_gbs"] if ach is not None else None, "traffic": None,
+            "note": "near-correction SpMV: 12 B per near pair (int32 column + FP64 value) + 8 B gathered density "
+                    "per pair and density, VtV + VtB, vs the measured copy bandwidth",
+            "ms_per_step": float(sums_ms), "near_pairs": nnz, "bytes": byts}
+
+
 def max_over_ranks(ms: float, device="cuda") -> float:
     """The slowest rank's step time (all ranks call it; 1 rank: unchanged)."""
     import torch
@@ -421,6 +438,7 @@ def run_ours(args):
             "stages_ms": {"vtv": [float(x) for x in sv], "vtb": [float(x) for x in sb],
                           "names": ["weights+clear", "P2M+M2M", "M2L", "L2L", "L2P+P2P", "sums+corrections"]},
             "roofline_other": roof_m2l if dominant is roof_p2p else roof_p2p,
+            "roofline_spmv": spmv_roofline(st, float(sv[5] + sb[5]), int(f.shape[0]), pk),
             "cpu_baseline": {"value": osamp_pts / osec, "unit": "target pts/s", "cores": cores, "kind": "oracle",
                              "sample": f"O1 direct definition on {len(tv)} VtV + {len(tb)} VtB sampled target "
                                        f"elements of the same workload ({osec:.1f} s)"},

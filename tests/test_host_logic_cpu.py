@@ -103,3 +103,17 @@ def test_blob_layout_matches_the_header():
     body = np.frombuffer(blob[32:], np.float32).reshape(3, 6032 + 32)
     assert np.array_equal(body[1, :6032], P) and np.array_equal(body[1, 6032:], eps)
     assert np.all(body[0, :6032] == 0) and np.all(np.isinf(body[0, 6032:]))      # absent networks: never used
+
+
+def test_spmv_roofline_counts_the_near_pairs_of_both_tasks():
+    """The bench's roofline of the near-correction SpMV: 12 B per near pair
+    plus 8 B per pair and density over the stage time, VtV and VtB together;
+    no stage time gives no figure instead of a division by zero."""
+    import bench
+    st = {"vtv": {"near_pairs": 1000}, "vtb": {"near_pairs": 24}, "btv": {"near_pairs": 7}}
+    r = bench.spmv_roofline(st, 0.002, 2, {"hbm_gbs": 5000.0})
+    assert r["near_pairs"] == 1024 and r["bytes"] == 1024 * (12 + 16)
+    assert r["achieved"] == pytest.approx(1024 * 28 / 2e-6 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / 5000.0)
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert bench.spmv_roofline({}, 0.0, 1, {"hbm_gbs": 5000.0})["achieved"] is None
